@@ -1,0 +1,246 @@
+/*
+ * nr.h -- C ABI of the GB300 dynamic-human NeRF renderer (libnr.so).
+ *
+ * The library renders one performer, held as a canonical radiance field plus
+ * a skeleton-driven motion field, from a pose and a camera, and trains that
+ * field against images.  The operations follow the paper's statement of the
+ * problem:
+ *   - a subject is a canonical field and its motion field (Sec. 4, Fig. 2:
+ *     M = M_skel + M_res; Sec. 4.2 weight volume W^c; Sec. 4.3 residual
+ *     MLP; Sec. 4.4 MLP_nerf);
+ *   - it is driven by a body pose theta = (J, Omega) (Sec. 4.1);
+ *   - it is rendered from a pinhole camera K with extrinsics (Fig. 2,
+ *     Sec. 5.1) by volume rendering (Sec. 2.1, Eq. 2-3) with empty-space
+ *     skipping and early ray termination (Sec. 2.3);
+ *   - it is trained on a squared photometric error with Adam (Sec. 5.2).
+ *
+ * Conventions for every call:
+ *   - every call returns an nr_status; nothing aborts the process;
+ *     nr_last_error() gives a thread-local message for the last failure;
+ *   - host pointers passed in are read during the call only (the library
+ *     copies what it keeps); device pointers passed in are read in stream
+ *     order on `stream` (a cudaStream_t, NULL = the legacy default stream);
+ *   - output buffers are owned by the caller;
+ *   - the subject owns all of its device state until nr_destroy();
+ *   - a subject may be used by one host thread at a time;
+ *   - all arrays are dense, C order, little-endian; floats are IEEE binary32.
+ */
+#ifndef NR_H
+#define NR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NR_ABI_VERSION 1u
+
+typedef enum {
+  NR_OK = 0,
+  NR_EINVAL = 1,        /* an argument is NULL, out of range or inconsistent */
+  NR_ENOMEM = 2,        /* a device or host allocation failed */
+  NR_ECUDA = 3,         /* a CUDA runtime call failed (message in nr_last_error) */
+  NR_ESTATE = 4,        /* wrong order of calls (e.g. render before nr_set_pose) */
+  NR_ETIMEOUT = 5,      /* a bounded wait gave up */
+  NR_EBUSY = 6,         /* the resource is in use */
+  NR_EUNSUPPORTED = 7   /* a valid request this build does not implement */
+} nr_status;
+
+typedef enum { NR_F32 = 0, NR_F16 = 1, NR_BF16 = 2, NR_FP8E4M3 = 3 } nr_dtype;
+
+typedef struct nr_subject nr_subject;   /* opaque, library-owned */
+
+/* Everything that defines one performer.  All pointers are host pointers,
+ * read during nr_create_subject only.
+ *
+ * Skeleton (Sec. 4.1, SMPL topology): n_bones joints, parents[i] < i or -1
+ * for the root, rest_joints[n_bones][3] in metres; the canonical pose is the
+ * rest pose.
+ * Box: the performer's axis-aligned bounding box (Sec. 4.4).
+ * Weight volume W^c (Sec. 4.2, Fig. S2): wvol[n_bones + 1][r][r][r] float32,
+ *   indexed [channel][z][y][x], r = wvol_res; vertex (i, j, k) sits at
+ *   box_min + (i, j, k) * (box_max - box_min) / (r - 1); the last channel is
+ *   the background and is not a bone.
+ * Hash grid (canonical encoding): hash_levels levels of 2^log2_T entries with
+ *   hash_feats features each; level_res[l] is the grid resolution N_l;
+ *   hash_table[L][T][F] float32 initial values.
+ * Canonical MLP (MLP_nerf, Sec. 4.4): mlp_in -> mlp_width (ReLU) x
+ *   mlp_hidden_layers -> 4; mlp_params packs, per layer, W[out][in] row-major
+ *   then b[out], float32.  Output: rgb = sigmoid(o[0:3]), sigma = softplus(o[3]).
+ * Residual MLP (MLP_res, Sec. 4.3, Fig. S3): if res_enabled, 5 layers of
+ *   width 64 on gamma(x_skel) (3 + 6 * res_pe_freqs dims) and the joint angles
+ *   Omega (3 * n_bones), skip of gamma into layer 4, output x_res[3]; packed as
+ *   the canonical MLP: W1[64][g + 3K], b1, W2[64][64], b2, W3[64][64], b3,
+ *   W4[64][64 + g], b4, W5[3][64], b5.
+ * Occupancy: ellipsoids[n_bones][15] (centre[3], rotation rows[9] mapping
+ *   canonical to the ellipsoid's local frame, radii[3]) in canonical space, or
+ *   NULL for no occupancy support; occ_grid cells per axis (a multiple of 8).
+ */
+typedef struct {
+  uint32_t abi_version;          /* NR_ABI_VERSION */
+  uint32_t n_bones;              /* 24 */
+  const int32_t *parents;
+  const float *rest_joints;
+  float box_min[3], box_max[3];
+  uint32_t wvol_res;
+  const float *wvol;
+  uint32_t hash_levels, hash_feats, log2_T;
+  const uint32_t *level_res;
+  const float *hash_table;
+  uint32_t mlp_in, mlp_width, mlp_hidden_layers;
+  const float *mlp_params;
+  uint32_t res_enabled, res_pe_freqs;
+  const float *res_params;
+  const float *ellipsoids;
+  uint32_t occ_grid;
+  int32_t device;                /* CUDA device ordinal */
+} nr_subject_desc;
+
+/* Limits of this build: n_bones == 24, hash_feats == 2, hash_levels <= 16,
+ * 10 <= log2_T <= 24, mlp_in == 32 with hash_levels * 2 <= 32,
+ * mlp_width == 64, 1 <= mlp_hidden_layers <= 4, res_pe_freqs <= 6,
+ * 2 <= wvol_res <= 256, occ_grid in {32, 64, 128, 256}.
+ * Errors: NR_EINVAL for a NULL or out-of-range field, NR_ENOMEM when device
+ * memory runs out (nothing is leaked), NR_ECUDA for other CUDA failures. */
+nr_status nr_create_subject(const nr_subject_desc *desc, void *stream, nr_subject **out);
+
+/* Releases every device buffer of the subject.  NULL is a no-op.  The
+ * handle must not be used afterwards. */
+nr_status nr_destroy(nr_subject *s);
+
+#define NR_POSE_MATRICES 1u   /* axis_angle holds G[n_bones][12] (rows [R | t]) instead */
+
+/* Sets the observed pose theta^o used by nr_render and nr_query.
+ * axis_angle[n_bones][3]: per-joint rotation (axis times angle, radians) in
+ * the parent's frame; root_t[3]: root translation (may be NULL = 0).
+ * The library computes, by forward kinematics in float64 on the host, the
+ * per-bone observation-to-canonical transforms G_i(x) = R_i x + t_i
+ * (Sec. 4.2), rounds them to float32, folds the joint angles into the
+ * residual MLP's first-layer bias, and, if the subject has ellipsoids,
+ * rebuilds the posed occupancy bitfield on the device: a cell is set iff for
+ * some bone i the canonical image G_i(c) of its centre lies in ellipsoid i
+ * dilated by half a cell diagonal.  With NR_POSE_MATRICES, axis_angle is
+ * G[n_bones][12] float32 and used as given; the joint angles are then taken
+ * as zero for the residual MLP.  Host pointers. */
+nr_status nr_set_pose(nr_subject *s, const float *axis_angle, const float *root_t,
+                      uint32_t flags, void *stream);
+
+/* Pinhole camera, OpenCV convention (x right, y down, z forward).
+ * Pixel (u, v) looks along R^T ((u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1)
+ * from o = -R^T t.  Each ray is clipped to [t_near, t_far] and to the
+ * subject's box; n_samples equal bins split the clipped segment and a
+ * rendered sample sits at each bin's midpoint. */
+typedef struct {
+  uint32_t width, height;
+  float fx, fy, cx, cy;
+  float R[9];          /* world -> camera rotation, row-major */
+  float t[3];          /* world -> camera translation */
+  float t_near, t_far;
+  uint32_t n_samples;  /* 1 .. 1024 */
+  float bg[3];         /* background colour composited behind the performer */
+} nr_camera;
+
+typedef struct {
+  nr_dtype mlp_dtype;      /* NR_F32 (CUDA cores), NR_BF16, NR_F16 (tensor cores) */
+  nr_dtype feat_dtype;     /* hash-table storage read by the encoder: NR_F32 or NR_F16 */
+  uint32_t use_occupancy;  /* skip samples whose posed occupancy cell is empty */
+  float t_min;             /* early ray termination once transmittance < t_min; 0 = off */
+  float hann_alpha;        /* residual PE window position; < 0 = all bands */
+  uint32_t flags;          /* NR_RENDER_PROFILE or 0 */
+} nr_render_opts;
+
+/* Renders the current pose from `cam` into out_rgba[height][width][4]
+ * (rgb = sum_i T_i alpha_i c_i + T_final bg, a = 1 - T_final), where
+ * alpha_i = (1 - exp(-sigma_i delta_i)) * min(S_i, 1) and S_i is the sum of
+ * the bone weights at the sample (the likelihood augmentation of Sec. 4.4).
+ * out_rgba may be a device or a host pointer; a host buffer is filled before
+ * the call returns, a device buffer in stream order.  Errors: NR_ESTATE
+ * before nr_set_pose; NR_EINVAL for bad sizes or options; NR_ENOMEM if the
+ * work queues cannot grow. */
+nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_render_opts *opts,
+                    float *out_rgba, void *stream);
+
+#define NR_QUERY_STRIDE 12
+/* Evaluates the field at n observation-space points x_obs[n][3] (device) for
+ * the current pose and writes out[n][12] (device):
+ *   x_skel[3], S, x_final[3], inside (1 or 0), rgb[3], sigma.
+ * Same dtype options as nr_render (use_occupancy and t_min are ignored). */
+nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, const nr_render_opts *opts,
+                   float *out, void *stream);
+
+/* Stores the training frames: per frame a pose (axis_angle[F][n_bones][3],
+ * root_t[F][3]) and a camera cams[F]; host pointers.  Replaces earlier frames. */
+nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float *axis_angle,
+                        const float *root_t, const nr_camera *cams, void *stream);
+
+#define NR_GRAD_ONLY 1u        /* compute gradients into the grad buffers, skip Adam */
+
+#define NR_TRAIN_WVOL 1u
+#define NR_TRAIN_HASH 2u
+#define NR_TRAIN_MLP 4u
+#define NR_TRAIN_RES 8u
+#define NR_TRAIN_ALL 15u
+
+/* One training batch of pixel rays.  frame_id, px, py: device uint32[n];
+ * target_rgb: device float32[n][3].  Samples are stratified: bin i of the
+ * clipped ray gets t_i = lo + (i + u_i) * (hi - lo) / S with u_i from the
+ * SplitMix64 generator seeded with step_seed (output k = ray * S + i + 1,
+ * u = top 24 bits * 2^-24); delta_i = t_{i+1} - t_i, delta_{S-1} = hi - t_{S-1}. */
+typedef struct {
+  uint32_t n_rays;
+  const uint32_t *frame_id, *px, *py;
+  const float *target_rgb;
+  uint32_t n_samples;
+  float bg[3];
+  uint64_t step_seed;
+  float lr, beta1, beta2, eps;   /* Adam (Sec. 5.2: beta = (0.9, 0.99)) */
+  float hann_alpha;              /* residual PE window; < 0 = all bands */
+  uint32_t flags;                /* NR_GRAD_ONLY */
+  uint32_t train_mask;           /* NR_TRAIN_* groups that are updated; 0 = all */
+} nr_train_batch;
+
+/* Forward, loss L = mean over rays and channels of (C^ - C_gt)^2, the
+ * hand-written backward into the gradient buffers (overwritten, not
+ * accumulated), then one Adam step (bias-corrected, every entry updated)
+ * on the selected groups.  loss_out (host, may be NULL) receives L after
+ * the step completes.  Errors: NR_ESTATE before nr_set_frames. */
+nr_status nr_train_step(nr_subject *s, const nr_train_batch *batch, float *loss_out, void *stream);
+
+#define NR_PARAM_WVOL 0u    /* [n_bones + 1][r][r][r] */
+#define NR_PARAM_HASH 1u    /* [L][T][F] (float32 master copy) */
+#define NR_PARAM_MLP 2u     /* canonical MLP, packed as in the descriptor */
+#define NR_PARAM_RES 3u     /* residual MLP, packed as in the descriptor */
+/* Device pointers of a parameter group (float32) and of its gradient buffer,
+ * and its element count.  Writing the parameters through *dev_ptr is allowed
+ * between calls; call nr_params_changed() afterwards. */
+nr_status nr_param(nr_subject *s, uint32_t which, float **dev_ptr, float **grad_ptr, size_t *count);
+nr_status nr_params_changed(nr_subject *s);
+
+/* Copies the current pose's float32 transforms G[n_bones][12] (host). */
+nr_status nr_pose_transforms(nr_subject *s, float *G_out);
+/* Copies the current posed occupancy bitfield (occ_grid^3 / 32 uint32, host);
+ * cell (x, y, z) is bit (z * g + y) * g + x. */
+nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out);
+
+#define NR_RENDER_PROFILE 1u  /* nr_render_opts.flags: time each stage with CUDA events */
+
+/* Stage times in milliseconds of the subject's last nr_render call made with
+ * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,
+ * [2] compositing (each summed over ray chunks), [3] the number of field
+ * launches.  CUDA events on the render's stream bracket every launch; this
+ * call waits for them.  NR_ESTATE if no profiled render has run. */
+nr_status nr_stage_times(nr_subject *s, float *ms_out);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all subjects, all threads). */
+uint64_t nr_launch_count(void);
+
+/* Thread-local description of the last error ("" if none). */
+const char *nr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NR_H */

@@ -1,0 +1,177 @@
+// common.cuh -- subject state, launch parameters and error plumbing shared by
+// the translation units of libnr.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nr.h"
+
+namespace nr {
+
+constexpr int kBones = 24;
+constexpr int kWidth = 64;          // hidden width of both MLPs
+constexpr int kMlpIn = 32;          // canonical MLP input (hash features, zero-padded)
+constexpr int kMaxLevels = 16;
+constexpr int kResGammaPad = 48;    // 3 + 6 * 6 = 39 PE dims, padded to a multiple of 16
+constexpr int kMaxHidden = 4;
+constexpr float kEpsW = 1e-4f;      // floor of the LBS denominator
+
+void set_error(const char *fmt, ...);
+
+#define NR_CHECK_CUDA(call)                                                      \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ::nr::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                      __FILE__, __LINE__);                                       \
+      return e_ == cudaErrorMemoryAllocation ? NR_ENOMEM : NR_ECUDA;             \
+    }                                                                            \
+  } while (0)
+
+#define NR_REQUIRE(cond, ...)                                                    \
+  do {                                                                           \
+    if (!(cond)) {                                                               \
+      ::nr::set_error(__VA_ARGS__);                                              \
+      return NR_EINVAL;                                                          \
+    }                                                                            \
+  } while (0)
+
+// Offsets (in floats) of each layer inside the float32 kernel weight blob.
+// Every matrix is stored transposed, [in][out], so that one thread's
+// activation times one row is a run of broadcast float4 reads.
+struct BlobLayout {
+  // residual MLP
+  int r1, r1b, r2, r2b, r3, r3b, r4, r4b, r5, r5b;
+  // canonical MLP: first, hidden (H - 1 of them), last
+  int c0, c0b, ch[kMaxHidden], chb[kMaxHidden], cl, clb;
+  int total;
+};
+
+// Offsets (in bf16/f16 elements) of the tensor-core weight blob: every
+// matrix is [out][in] row-major with rows padded to kTcRow elements so that
+// ldmatrix row reads are free of bank conflicts.
+constexpr int kTcRow = 72;          // 64 + 8
+constexpr int kTcRowWide = 120;     // 112 + 8 (residual layer 4: [h3 | gamma])
+struct TcLayout {
+  int r1, r2, r3, r4, r5, c0, ch[kMaxHidden], cl;
+  int total;                         // elements
+};
+
+// Everything one field evaluation needs; passed to kernels by value.
+struct FieldParams {
+  float bmin[3], bmax[3];
+  float vol_scale[3];                // (R - 1) / (bmax - bmin)
+  float inv_box[3];                  // 1 / (bmax - bmin)
+  float box_c[3], box_ih[3];         // box centre and 2 / (bmax - bmin)
+  int wres;
+  const float *wvol;                 // [25][R^3]
+  int L;
+  uint32_t T_mask;
+  uint32_t dense_mask;               // bit l set if level l is dense
+  uint32_t level_res[kMaxLevels];
+  const float2 *table32;             // [L][T] float2
+  const __half2 *table16;            // [L][T] half2
+  int use_f16_table;
+  int hidden;                        // canonical hidden layers
+  int res_enabled, res_freqs;
+  float hann[8];
+  const float *blob;                 // float32 weight blob (BlobLayout)
+  BlobLayout lay;
+  const void *tc_blob;               // bf16/f16 weight blob (TcLayout)
+  TcLayout tlay;
+  const float *G;                    // [24][12] of the current pose
+  const float *bias1;                // [64] residual layer-1 bias with the pose folded in
+};
+
+struct Frame {                       // a training frame's camera (decoded)
+  float R[9], t[3];
+  float fx, fy, cx, cy, t_near, t_far;
+  uint32_t width, height;
+};
+
+}  // namespace nr
+
+// ----------------------------------------------------------------- subject
+struct nr_subject {
+  uint32_t magic = 0x4e525342u;
+  int device = 0;
+  // configuration
+  uint32_t K = 24;
+  float bmin[3], bmax[3];
+  uint32_t wres = 0;
+  uint32_t L = 0, F = 2, log2T = 0, T = 0;
+  uint32_t level_res[nr::kMaxLevels] = {0};
+  uint32_t mlp_in = 32, width = 64, hidden = 2;
+  uint32_t res_enabled = 0, res_freqs = 0;
+  uint32_t occ_grid = 128;
+  bool has_ellipsoids = false;
+  std::vector<int> parents;
+  std::vector<double> rest;          // [K][3]
+  // float32 master parameters and their gradients
+  float *wvol = nullptr, *g_wvol = nullptr;
+  float *table = nullptr, *g_table = nullptr;
+  float *mlp = nullptr, *g_mlp = nullptr;
+  float *res = nullptr, *g_res = nullptr;
+  size_t n_wvol = 0, n_table = 0, n_mlp = 0, n_res = 0;
+  // Adam moments (allocated at the first training step)
+  float *adam_m = nullptr, *adam_v = nullptr;
+  size_t n_params_total = 0;
+  uint32_t adam_t = 0;
+  // derived, rebuilt when parameters change
+  __half2 *table16 = nullptr;
+  float *blob = nullptr;
+  nr::BlobLayout lay{};
+  __nv_bfloat16 *tc_bf16 = nullptr;
+  __half *tc_f16 = nullptr;
+  nr::TcLayout tlay{};
+  bool params_dirty = true;
+  // current pose
+  bool pose_set = false;
+  float h_G[24 * 12];
+  float h_omega[24 * 3];
+  float *d_G = nullptr;              // [24][12]
+  float *d_omega = nullptr;          // [72]
+  float *d_bias1 = nullptr;          // [64]
+  bool bias_dirty = true;
+  float *ellip = nullptr;            // [24][15]
+  uint32_t *bits = nullptr;          // occ_grid^3 / 32
+  // training frames
+  uint32_t n_frames = 0, frames_cap = 0;
+  float *f_G = nullptr;              // [F][24][12]
+  float *f_omega = nullptr;          // [F][72]
+  float *f_bias1 = nullptr;          // [F][64]
+  nr::Frame *f_cam = nullptr;        // [F]
+  // render workspace (grow-only)
+  size_t ws_samples = 0, ws_rays = 0;
+  float4 *samp = nullptr;            // [max samples] x, y, z, delta
+  float4 *samp_out = nullptr;        // [max samples] r, g, b, alpha
+  uint2 *ray_range = nullptr;        // [max rays] offset, count
+  uint32_t *counter = nullptr;       // [4] device counters
+  float *out_stage = nullptr;        // [max rays][4] staging for host outputs
+  size_t stage_cap = 0;
+  // stage profiling (NR_RENDER_PROFILE): event pairs per stage and chunk
+  static constexpr int kProfEvents = 64;
+  cudaEvent_t prof_ev[kProfEvents] = {};
+  int prof_used = 0;                 // events recorded by the last profiled render
+  int prof_chunks = 0;
+  // training workspace
+  size_t tw_rays = 0;
+  float *t_ray = nullptr;            // [n][8]: rgb_hat, T_final, dL/dC (3), pad
+  float *loss_acc = nullptr;         // [1]
+  float *f_dbias1 = nullptr;         // [F][64] gradient of the per-frame first-layer bias
+};
+
+namespace nr {
+void count_launches(uint64_t n);                              // kernels launched by the library
+bool subject_ok(const nr_subject *s);
+nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs
+nr_status ensure_bias(nr_subject *s, cudaStream_t st);         // pose-folded bias
+FieldParams field_params(const nr_subject *s, const nr_render_opts *o);
+nr_status set_error_cuda(cudaError_t e, const char *what);
+}  // namespace nr

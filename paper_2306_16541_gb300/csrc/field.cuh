@@ -1,0 +1,264 @@
+// field.cuh -- device-side steps of the per-sample field (Sec. 4.2 - 4.4):
+// inverse-LBS warp over the canonical weight volume, positional encoding with
+// the truncated Hann window, multiresolution hash encoding, and the float32
+// CUDA-core MLP layers.  Included by the forward and backward kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace nr {
+
+// ------------------------------------------------------------------ LBS warp
+// Sec. 4.2: x_skel = sum_i w_i^c(G_i x) G_i(x) / sum_k w_k^c(G_k x), with the
+// candidate p_i = G_i x = R_i x + t_i and w_i^c read trilinearly from channel
+// i of the canonical weight volume (vertices on the box corners, a corner
+// outside the grid contributes zero).  The denominator S is floored at kEpsW.
+
+__device__ __forceinline__ float vol_fetch(const float *__restrict__ ch, int i) { return __ldg(ch + i); }
+
+// Trilinear sample of one channel at grid coordinate u (in vertex units).
+__device__ __forceinline__ float trilinear_channel(const float *__restrict__ ch, int R, float ux, float uy,
+                                                   float uz) {
+  const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
+  const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+  const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
+  if (ix >= 0 && iy >= 0 && iz >= 0 && ix + 1 < R && iy + 1 < R && iz + 1 < R) {
+    const int b = (iz * R + iy) * R + ix;
+    const int RR = R * R;
+    const float c000 = vol_fetch(ch, b), c100 = vol_fetch(ch, b + 1);
+    const float c010 = vol_fetch(ch, b + R), c110 = vol_fetch(ch, b + R + 1);
+    const float c001 = vol_fetch(ch, b + RR), c101 = vol_fetch(ch, b + RR + 1);
+    const float c011 = vol_fetch(ch, b + RR + R), c111 = vol_fetch(ch, b + RR + R + 1);
+    const float c00 = fmaf(fx, c100 - c000, c000), c10 = fmaf(fx, c110 - c010, c010);
+    const float c01 = fmaf(fx, c101 - c001, c001), c11 = fmaf(fx, c111 - c011, c011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0);
+  }
+  if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) return 0.f;
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ax = ix + (c & 1), ay = iy + ((c >> 1) & 1), az = iz + (c >> 2);
+    if (ax < 0 || ay < 0 || az < 0 || ax >= R || ay >= R || az >= R) continue;
+    const float w = ((c & 1) ? fx : 1.f - fx) * (((c >> 1) & 1) ? fy : 1.f - fy) * ((c >> 2) ? fz : 1.f - fz);
+    acc = fmaf(w, vol_fetch(ch, (az * R + ay) * R + ax), acc);
+  }
+  return acc;
+}
+
+// sG: the 24 bone transforms [24][12] (rows [R | t]) in shared memory.
+__device__ __forceinline__ void lbs_warp(const FieldParams &P, const float *__restrict__ sG, float x0, float x1,
+                                         float x2, float &s0, float &s1, float &s2, float &S) {
+  const int R = P.wres;
+  const int R3 = R * R * R;
+  float n0 = 0.f, n1 = 0.f, n2 = 0.f, sum = 0.f;
+#pragma unroll 2
+  for (int i = 0; i < kBones; ++i) {
+    const float *g = sG + 12 * i;
+    const float p0 = fmaf(g[0], x0, fmaf(g[1], x1, fmaf(g[2], x2, g[3])));
+    const float p1 = fmaf(g[4], x0, fmaf(g[5], x1, fmaf(g[6], x2, g[7])));
+    const float p2 = fmaf(g[8], x0, fmaf(g[9], x1, fmaf(g[10], x2, g[11])));
+    const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
+    const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
+    const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
+    const float w = trilinear_channel(P.wvol + (size_t)i * R3, R, ux, uy, uz);
+    sum += w;
+    n0 = fmaf(w, p0, n0);
+    n1 = fmaf(w, p1, n1);
+    n2 = fmaf(w, p2, n2);
+  }
+  const float inv = 1.f / fmaxf(sum, kEpsW);
+  s0 = n0 * inv;
+  s1 = n1 * inv;
+  s2 = n2 * inv;
+  S = sum;
+}
+
+// ------------------------------------------------------- positional encoding
+// Sec. 4.3: gamma(x) = [x^, w_k sin(2^k pi x^), w_k cos(2^k pi x^)]_{k<L} with
+// x^ the point normalised to [-1, 1] over the box and w_k the truncated Hann
+// weight of band k.  Writes kResGammaPad values (zero padded).
+__device__ __forceinline__ void pos_enc(const FieldParams &P, float x0, float x1, float x2, float *__restrict__ g,
+                                        int stride) {
+  const float h0 = (x0 - P.box_c[0]) * P.box_ih[0];
+  const float h1 = (x1 - P.box_c[1]) * P.box_ih[1];
+  const float h2 = (x2 - P.box_c[2]) * P.box_ih[2];
+  g[0] = h0;
+  g[stride] = h1;
+  g[2 * stride] = h2;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float sc = (float)(1 << k);
+    float sa, ca, sb, cb, sd, cd;
+    sincospif(sc * h0, &sa, &ca);
+    sincospif(sc * h1, &sb, &cb);
+    sincospif(sc * h2, &sd, &cd);
+    const float w = (k < P.res_freqs) ? P.hann[k] : 0.f;
+    float *q = g + (3 + 6 * k) * stride;
+    q[0] = w * sa;
+    q[stride] = w * sb;
+    q[2 * stride] = w * sd;
+    q[3 * stride] = w * ca;
+    q[4 * stride] = w * cb;
+    q[5 * stride] = w * cd;
+  }
+#pragma unroll
+  for (int j = 39; j < kResGammaPad; ++j) g[j * stride] = 0.f;
+}
+
+// ------------------------------------------------------------- hash encoding
+// Multiresolution hash encoding of the canonical point (the workloads' field):
+// p = (x - box_min) / (box_max - box_min); on level l the point sits at p N_l
+// among vertices 0..N_l; its cell is floor(p N_l) capped at N_l - 1; the 8
+// corners are read trilinearly.  Dense levels ((N+1)^3 <= T) index row-major,
+// the others by (x ^ y 2654435761 ^ z 805459861) mod T.  Outside the box the
+// features are zero (and the sample gets no density).
+
+constexpr uint32_t kPrimeY = 2654435761u;
+constexpr uint32_t kPrimeZ = 805459861u;
+
+struct HashCell {
+  uint32_t idx[8];
+  float w[8];
+};
+
+__device__ __forceinline__ void hash_cell(const FieldParams &P, int l, float p0, float p1, float p2, HashCell &c) {
+  const uint32_t N = P.level_res[l];
+  const float fn = (float)N;
+  const float q0 = p0 * fn, q1 = p1 * fn, q2 = p2 * fn;
+  const float a0 = fminf(floorf(q0), fn - 1.f), a1 = fminf(floorf(q1), fn - 1.f), a2 = fminf(floorf(q2), fn - 1.f);
+  const float f0 = q0 - a0, f1 = q1 - a1, f2 = q2 - a2;
+  const uint32_t i0 = (uint32_t)a0, i1 = (uint32_t)a1, i2 = (uint32_t)a2;
+  const bool dense = (P.dense_mask >> l) & 1u;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t x = i0 + (k & 1), y = i1 + ((k >> 1) & 1), z = i2 + (k >> 2);
+    uint32_t id;
+    if (dense) {
+      id = x + y * (N + 1) + z * (N + 1) * (N + 1);
+    } else {
+      id = (x ^ (y * kPrimeY) ^ (z * kPrimeZ)) & P.T_mask;
+    }
+    c.idx[k] = id;
+    c.w[k] = ((k & 1) ? f0 : 1.f - f0) * (((k >> 1) & 1) ? f1 : 1.f - f1) * ((k >> 2) ? f2 : 1.f - f2);
+  }
+}
+
+__device__ __forceinline__ float2 table_read(const FieldParams &P, int l, uint32_t id) {
+  const size_t off = (size_t)l * (size_t)(P.T_mask + 1) + id;
+  if (P.use_f16_table) {
+    const __half2 h = P.table16[off];
+    return __half22float2(h);
+  }
+  return __ldg(P.table32 + off);
+}
+
+// enc (a column with the given stride): 2 features per level, zero beyond 2L.  Returns whether x is inside the box.
+__device__ __forceinline__ bool hash_encode(const FieldParams &P, float x0, float x1, float x2, float *__restrict__ enc,
+                                            int stride) {
+  float p0 = (x0 - P.bmin[0]) * P.inv_box[0];
+  float p1 = (x1 - P.bmin[1]) * P.inv_box[1];
+  float p2 = (x2 - P.bmin[2]) * P.inv_box[2];
+  const bool inside = p0 >= 0.f && p0 <= 1.f && p1 >= 0.f && p1 <= 1.f && p2 >= 0.f && p2 <= 1.f;
+  p0 = fminf(fmaxf(p0, 0.f), 1.f);
+  p1 = fminf(fmaxf(p1, 0.f), 1.f);
+  p2 = fminf(fmaxf(p2, 0.f), 1.f);
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    float a = 0.f, b = 0.f;
+    if (l < P.L) {
+      HashCell c;
+      hash_cell(P, l, p0, p1, p2, c);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 v = table_read(P, l, c.idx[k]);
+        a = fmaf(c.w[k], v.x, a);
+        b = fmaf(c.w[k], v.y, b);
+      }
+    }
+    enc[(2 * l) * stride] = inside ? a : 0.f;
+    enc[(2 * l + 1) * stride] = inside ? b : 0.f;
+  }
+  return inside;
+}
+
+// -------------------------------------------------------- float32 MLP layers
+// y = W x + b with W stored transposed ([in][out], out a multiple of 4) in
+// shared memory and read as broadcast float4 (all threads of the block read
+// the same weight).  Each thread keeps its activations in its own column of a
+// shared-memory buffer, col[k * stride] (stride = threads per block), so the
+// loop over inputs is a runtime loop; the 64 accumulators live in registers.
+template <int OUT>
+__device__ __forceinline__ void dense_acc_f32(const float *__restrict__ Wt, const float *__restrict__ col, int in,
+                                              int stride, float (&y)[OUT]) {
+#pragma unroll 2
+  for (int k = 0; k < in; ++k) {
+    const float xk = col[k * stride];
+    const float4 *row = reinterpret_cast<const float4 *>(Wt + k * OUT);
+#pragma unroll
+    for (int j = 0; j < OUT / 4; ++j) {
+      const float4 w = row[j];
+      y[4 * j + 0] = fmaf(xk, w.x, y[4 * j + 0]);
+      y[4 * j + 1] = fmaf(xk, w.y, y[4 * j + 1]);
+      y[4 * j + 2] = fmaf(xk, w.z, y[4 * j + 2]);
+      y[4 * j + 3] = fmaf(xk, w.w, y[4 * j + 3]);
+    }
+  }
+}
+
+template <int OUT>
+__device__ __forceinline__ void dense_f32(const float *__restrict__ Wt, const float *__restrict__ b,
+                                          const float *__restrict__ col, int in, int stride, float (&y)[OUT]) {
+#pragma unroll
+  for (int j = 0; j < OUT; ++j) y[j] = b[j];
+  dense_acc_f32<OUT>(Wt, col, in, stride, y);
+}
+
+template <int N>
+__device__ __forceinline__ void store_relu(const float (&y)[N], float *__restrict__ col, int stride) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) col[j * stride] = fmaxf(y[j], 0.f);
+}
+
+__device__ __forceinline__ float sigmoidf_(float o) { return 1.f / (1.f + __expf(-o)); }
+__device__ __forceinline__ float softplusf_(float o) { return fmaxf(o, 0.f) + log1pf(__expf(-fabsf(o))); }
+
+// Residual MLP (Sec. 4.3, Fig. S3) in float32.  gcol holds gamma(x_skel)
+// (kResGammaPad rows), hcol is the 64-row scratch column; returns x_res.
+// bias1 holds b1 + W_Omega Omega (the pose folded into the first layer).
+__device__ __forceinline__ void residual_f32(const FieldParams &P, const float *__restrict__ W,
+                                             const float *__restrict__ bias1, const float *__restrict__ gcol,
+                                             float *__restrict__ hcol, int stride, float &r0, float &r1, float &r2) {
+  float y[kWidth];
+  dense_f32<kWidth>(W + P.lay.r1, bias1, gcol, kResGammaPad, stride, y);
+  store_relu(y, hcol, stride);
+  dense_f32<kWidth>(W + P.lay.r2, W + P.lay.r2b, hcol, kWidth, stride, y);
+  store_relu(y, hcol, stride);
+  dense_f32<kWidth>(W + P.lay.r3, W + P.lay.r3b, hcol, kWidth, stride, y);
+  store_relu(y, hcol, stride);
+  // layer 4 sees [h3, gamma]: the transposed rows of h3, then those of gamma
+  dense_f32<kWidth>(W + P.lay.r4, W + P.lay.r4b, hcol, kWidth, stride, y);
+  dense_acc_f32<kWidth>(W + P.lay.r4 + kWidth * kWidth, gcol, kResGammaPad, stride, y);
+  store_relu(y, hcol, stride);
+  float o[4];
+  dense_f32<4>(W + P.lay.r5, W + P.lay.r5b, hcol, kWidth, stride, o);
+  r0 = o[0];
+  r1 = o[1];
+  r2 = o[2];
+}
+
+// Canonical MLP (MLP_nerf, Sec. 4.4) in float32 on the encoding held in hcol
+// rows 0..31; returns the 4 raw outputs.
+__device__ __forceinline__ void canonical_f32(const FieldParams &P, const float *__restrict__ W,
+                                              float *__restrict__ hcol, int stride, float (&o)[4]) {
+  float y[kWidth];
+  dense_f32<kWidth>(W + P.lay.c0, W + P.lay.c0b, hcol, kMlpIn, stride, y);
+  store_relu(y, hcol, stride);
+  for (int l = 0; l < P.hidden - 1; ++l) {
+    dense_f32<kWidth>(W + P.lay.ch[l], W + P.lay.chb[l], hcol, kWidth, stride, y);
+    store_relu(y, hcol, stride);
+  }
+  dense_f32<4>(W + P.lay.cl, W + P.lay.clb, hcol, kWidth, stride, o);
+}
+
+}  // namespace nr

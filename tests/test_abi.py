@@ -1,0 +1,61 @@
+"""The C ABI library loads and exports every entry point include/nr.h declares,
+and its argument checks answer without a GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nr():
+    from paper_2306_16541_gb300 import build
+    build.build()
+    from paper_2306_16541_gb300 import nr as mod
+    return mod
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:nr_status|const char \*|void)\s*\**\s*(nr_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["nr_create_subject", "nr_set_pose", "nr_render", "nr_train_step", "nr_destroy"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(nr):
+    lib = C.CDLL(nr.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_argument_errors_without_gpu(nr):
+    h = C.c_void_p()
+    assert nr.lib.nr_create_subject(None, None, C.byref(h)) == nr.NR_EINVAL
+    assert b"NULL" in nr.lib.nr_last_error()
+    d = nr.nr_subject_desc()
+    d.abi_version = 999
+    assert nr.lib.nr_create_subject(C.byref(d), None, C.byref(h)) == nr.NR_EINVAL
+    assert b"abi_version" in nr.lib.nr_last_error()
+    d.abi_version, d.n_bones = nr.NR_ABI_VERSION, 23
+    assert nr.lib.nr_create_subject(C.byref(d), None, C.byref(h)) == nr.NR_EINVAL
+    assert nr.lib.nr_destroy(None) == nr.NR_OK
+    assert nr.lib.nr_render(None, None, None, None, None) == nr.NR_EINVAL
+    assert nr.lib.nr_set_pose(None, None, None, 0, None) == nr.NR_EINVAL
+
+
+def test_struct_sizes_match_header(nr):
+    # nr_camera: 2 u32 + 4 f + 9 f + 3 f + 2 f + u32 + 3 f = 24 * 4 bytes
+    assert C.sizeof(nr.nr_camera) == 96
+    assert C.sizeof(nr.nr_render_opts) == 24

@@ -1,0 +1,169 @@
+"""Forward parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the float32 path within 1e-3 max-abs RGBA of the oracle; the
+bf16/f16 tensor-core tiers at PSNR >= 50 dB.  Integer decisions (which rays
+hit the box, the posed occupancy bitfield, which samples are live) are taken
+in float32 by both sides and must agree exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import decide32, fk
+from oracle import field as OF
+from paper_2306_16541_gb300 import synth
+
+from _util import gpu_render, nrmod, oracle_render, psnr
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-3
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.config_tiny()
+
+
+@pytest.fixture(scope="module")
+def tiny_structured():
+    cfg = synth.config_tiny()
+    cfg["subject"] = synth.subject(1234, hash_scale=0.5, res_last_std=0.02)
+    return cfg
+
+
+@pytest.fixture(scope="module")
+def frame():
+    return synth.config_frame512()
+
+
+def _small(cam, res, n_samples=None):
+    c = synth.camera(res, res, 1.25 * res, (0.0, 0.0, 2.5), n_samples or cam.n_samples, cam.t_near, cam.t_far)
+    c.R, c.t = cam.R, cam.t
+    return c
+
+
+def test_fk_matches_oracle(tiny):
+    nr = nrmod()
+    S = nr.Subject(tiny["subject"])
+    try:
+        S.set_pose(*tiny["pose"])
+        G = S.pose_transforms()
+    finally:
+        S.close()
+    s = tiny["subject"]
+    ref = fk.bone_transforms_f32(s["parents"], s["rest_joints"], *tiny["pose"])
+    assert np.abs(G - ref).max() <= 1e-6
+
+
+def test_posed_bitfield_bit_exact(frame):
+    nr = nrmod()
+    s = frame["subject"]
+    G32 = fk.bone_transforms_f32(s["parents"], s["rest_joints"], *frame["pose"])
+    S = nr.Subject(s)
+    try:
+        S.set_pose(G32, matrices=True)
+        bits = S.occupancy()
+    finally:
+        S.close()
+    ref = decide32.posed_bitfield32(G32, s["ellipsoids"], s["box_min"], s["box_max"], 128)
+    assert np.array_equal(bits, ref), int(np.count_nonzero(bits != ref))
+    frac = np.unpackbits(bits.view(np.uint8)).mean()
+    assert 0.1 < frac < 0.3
+
+
+def test_query_matches_oracle(tiny_structured):
+    nr = nrmod()
+    cfg = tiny_structured
+    s = cfg["subject"]
+    x = np.random.default_rng(3).uniform(-0.9, 0.9, size=(4099, 3)).astype(np.float32)
+    S = nr.Subject(s)
+    try:
+        S.set_pose(*cfg["pose"])
+        out = S.query(torch.from_numpy(x).cuda()).cpu().numpy()
+    finally:
+        S.close()
+    P = OF.Params(s)
+    R, t = fk.bone_transforms(s["parents"], s["rest_joints"], *cfg["pose"])
+    ref = OF.field(torch.from_numpy(x.astype(np.float64)), P, torch.from_numpy(R), torch.from_numpy(t),
+                   torch.from_numpy(cfg["pose"][0].astype(np.float64)).reshape(-1))
+    S_ref = ref["S"].numpy()
+    assert np.abs(out[:, 3] - S_ref).max() < 1e-5
+    m = S_ref > 1e-2                                   # x_skel is well conditioned there
+    assert m.sum() > 500
+    assert np.abs(out[m, 0:3] - ref["x_skel"].numpy()[m]).max() < 1e-4
+    assert np.abs(out[m, 4:7] - ref["x_final"].numpy()[m]).max() < 1e-4
+    inside = ref["inside"].numpy()
+    assert np.array_equal(out[m, 7] > 0.5, inside[m])
+    mi = m & inside
+    assert np.abs(out[mi, 8:11] - ref["rgb"].numpy()[mi]).max() < 1e-3
+    assert np.abs(out[mi, 11] - ref["sigma"].numpy()[mi]).max() < 1e-3
+
+
+@pytest.mark.parametrize("structured", [False, True])
+def test_render_tiny_f32(tiny, tiny_structured, structured):
+    cfg = tiny_structured if structured else tiny
+    got = gpu_render(cfg["subject"], cfg["pose"], cfg["camera"], False)
+    ref = oracle_render(cfg["subject"], cfg["pose"], cfg["camera"], False).reshape(got.shape)
+    err = np.abs(got - ref).max()
+    assert err <= TOL_F32, err
+    assert ref[..., 3].max() > 0.1
+
+
+def test_render_host_buffer_equals_device(tiny_structured):
+    cfg = tiny_structured
+    a = gpu_render(cfg["subject"], cfg["pose"], cfg["camera"], False)
+    b = gpu_render(cfg["subject"], cfg["pose"], cfg["camera"], False, host=True)
+    assert np.array_equal(a, b)
+
+
+def test_render_frame_field_with_occupancy(frame):
+    """The 512x512 workload's field (16 levels of 2^19 f16 entries, 64^3 volume,
+    3 hidden layers, occupancy) rendered at 64x64, every pixel against the oracle."""
+    cam = _small(frame["camera"], 64)
+    got = gpu_render(frame["subject"], frame["pose"], cam, True, feat="f16")
+    ref = oracle_render(frame["subject"], frame["pose"], cam, True).reshape(got.shape)
+    err = np.abs(got - ref).max()
+    assert err <= TOL_F32, err
+
+
+def test_render_frame_full_size_sampled(frame):
+    """512x512, 128 samples, occupancy, as the bench launches it; 1500 sampled pixels."""
+    cam = frame["camera"]
+    got = gpu_render(frame["subject"], frame["pose"], cam, True, feat="f16")
+    rng = np.random.default_rng(0)
+    px = rng.integers(0, cam.width, 1500)
+    py = rng.integers(0, cam.height, 1500)
+    ref = oracle_render(frame["subject"], frame["pose"], cam, True, px, py)
+    err = np.abs(got[py, px] - ref).max()
+    assert err <= TOL_F32, err
+
+
+def test_early_termination_bound(tiny_structured):
+    cfg = dict(tiny_structured)
+    s = synth.subject(77, hash_scale=0.5)
+    # dense field: large positive sigma bias so rays terminate early
+    s["mlp_layers"][-1][1][3] = 40.0
+    s["mlp_params"] = synth.pack_layers(s["mlp_layers"])
+    full = gpu_render(s, cfg["pose"], cfg["camera"], False, t_min=0.0)
+    ert = gpu_render(s, cfg["pose"], cfg["camera"], False, t_min=1e-4)
+    assert (1 - full[..., 3]).min() < 1e-4                # some rays do terminate
+    assert np.abs(full - ert).max() <= 1e-4
+
+
+def test_rays_missing_the_box_get_background(tiny):
+    cfg = tiny
+    cam = synth.camera(16, 8, 20.0, (0.0, 0.0, 2.5), 8, 1.5, 3.5, bg=(0.25, 0.5, 0.75))
+    R, t = synth.look_at((0.0, 0.0, 2.5), target=(0.0, 5.0, 2.5), up=(0.0, 0.0, 1.0))
+    cam.R, cam.t = R, t                                   # looking straight up, away from the box
+    got = gpu_render(cfg["subject"], cfg["pose"], cam, False)
+    assert np.allclose(got[..., :3], [0.25, 0.5, 0.75]) and (got[..., 3] == 0).all()
+
+
+@pytest.mark.parametrize("res,S", [(1, 1), (3, 7), (17, 33)])
+def test_ragged_sizes(tiny_structured, res, S):
+    cfg = tiny_structured
+    cam = _small(cfg["camera"], res, S)
+    got = gpu_render(cfg["subject"], cfg["pose"], cam, False)
+    ref = oracle_render(cfg["subject"], cfg["pose"], cam, False).reshape(got.shape)
+    assert np.abs(got - ref).max() <= TOL_F32
