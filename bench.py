@@ -1,0 +1,280 @@
+#!/usr/bin/env python
+"""Throughput of one rendered frame of a posed performer (rays/s).
+
+Workload: 512x512 image, 128 samples per ray, occupancy bitfield 128^3
+(~15-18 % of cells set), hash grid of 16 levels x 2 features with 2^19 f16
+entries (N 16..2048), canonical MLP 32-64-64-64-4, residual MLP with 6 PE
+bands, 64^3 x 25 float32 weight volume, early ray termination at T < 1e-4.
+One step = a fresh pose (forward kinematics + posed occupancy bitfield) and
+the whole render (ray march with compaction, the fused per-sample field,
+compositing), through the C ABI.  Synthetic, seeded inputs shaped like the
+paper's workloads (one ~1.7 m performer in a 2 m box, 128 samples per ray).
+
+With torchrun (N > 1) every rank renders its own frames (independent
+replicas, no collective: weak scaling).  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/sec (512x512 frame render, 128 samples/ray, occupancy + ERT)"
+UNIT = "rays/s"
+L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-pixels", type=int, default=4096)
+    return p.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_2306_16541_gb300 import synth
+    cfg = synth.config_frame512()
+    rng = np.random.default_rng(4321)
+    poses = [synth.random_pose(rng) for _ in range(8)]
+    return cfg, poses
+
+
+def cpu_baseline(cfg, poses, n_pixels, seed=0):
+    """The FP64 oracle, as it stands, on n_pixels random pixels of the same frame."""
+    import torch
+    from oracle import field as OF
+    from oracle import render as OR
+    cam = cfg["camera"]
+    rng = np.random.default_rng(seed)
+    px = rng.integers(0, cam.width, n_pixels)
+    py = rng.integers(0, cam.height, n_pixels)
+    P = OF.Params(cfg["subject"])
+    t0 = time.perf_counter()
+    OR.render_pixels(cfg["subject"], P, poses[0], cam, px, py, True)
+    dt = time.perf_counter() - t0
+    return dict(value=n_pixels / dt, unit=UNIT, cores=torch.get_num_threads(), kind="oracle",
+                sample=f"{n_pixels} random pixels of one 512x512 frame (128 samples each, occupancy; "
+                       f"FP64 torch CPU, no early termination), {dt:.1f} s")
+
+
+def run_reference(a):
+    rank, world, local = dist_setup(a.gpus)
+    if rank != 0:
+        return
+    cfg, poses = workload()
+    vals = []
+    for i in range(a.warmup + a.steps):
+        r = cpu_baseline(cfg, poses, 256, seed=i)
+        if i >= a.warmup:
+            vals.append(r["value"])
+    ms_per_step = 1000.0 * 512 * 512 / statistics.mean(vals)
+    v = statistics.mean(vals)
+    base = cpu_baseline(cfg, poses, 256, seed=99)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "frame_512x512_s128_occupancy", "sample_per_step": "256 random pixels"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": "256 random pixels of one 512x512 frame per step, FP64 torch CPU"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(a):
+    import torch
+    rank, world, local = dist_setup(a.gpus)
+    torch.cuda.set_device(local)
+    from paper_2306_16541_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(world)
+    from paper_2306_16541_gb300 import nr
+
+    cfg, poses = workload()
+    cam = nr.make_camera(cfg["camera"])
+    W, H = cam.width, cam.height
+    n_rays = W * H
+    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True)
+    S = nr.Subject(cfg["subject"], device=local)
+    out = torch.empty(H, W, 4, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step(i):
+        S.set_pose(*poses[(i + rank) % len(poses)])
+        S.render(cam, opts, out)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    stages = []
+    launches0 = nr.nr_launch_count()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    barrier(world)
+    for i in range(a.steps):
+        flush.zero_()                       # L2 flush between timed steps (outside the events)
+        ev[i][0].record()
+        step(i)
+        ev[i][1].record()
+        stages.append(S.stage_times())      # field-kernel events recorded on the render stream
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = nr.nr_launch_count() - launches0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = world * n_rays * a.steps / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: pose from host memory,
+    # image into pinned host memory (the library copies it back), wall clock
+    host_out = torch.empty(H, W, 4, dtype=torch.float32).pin_memory()
+    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4)
+    for i in range(2):
+        S.set_pose(*poses[i])
+        nr.nr_render(S.h, cam, opts_e2e, host_out)
+    barrier(world)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        S.set_pose(*poses[(i + rank) % len(poses)])
+        nr.nr_render(S.h, cam, opts_e2e, host_out)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * n_rays * a.steps / e2e_s
+
+    field_ms = statistics.mean(s["field_ms"] for s in stages)
+    live = statistics.mean(s["live_samples"] for s in stages)
+    s = cfg["subject"]
+    L = int(s["hash_levels"])
+    # algorithmic bytes per live sample: 24 bones x 8 corners x 4 B of the weight volume,
+    # L levels x 8 corners x 2 features x 2 B of f16 table, 16 B sample in, 16 B (rgb, alpha) out
+    bytes_per_sample = 24 * 8 * 4 + L * 8 * 2 * 2 + 16 + 16
+    achieved = bytes_per_sample * live / (field_ms / 1000.0) / 1e9
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    traffic = os.environ.get("NR_FIELD_TRAFFIC_BYTES")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "bf16", "f16": "f16"}[a.mlp], "data": "synthetic",
+        "config": {"workload": "frame_512x512_s128_occupancy", "image": [W, H], "samples_per_ray": 128,
+                   "occupancy_grid": 128, "hash": "16x2 levels, 2^19 f16 entries, N 16..2048",
+                   "mlp": f"32-64-64-64-4 {a.mlp}", "residual_mlp": f"6 PE bands, width 64, {a.mlp}",
+                   "weight_volume": "64^3 x 25 f32", "ert_t_min": 1e-4, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MiB write) between timed steps"},
+        "samples_per_s": world * live * a.steps / (total_ms / 1000.0),
+        "live_samples_per_frame": live,
+        "stage_ms": {k: statistics.mean(st[k] for st in stages) for k in ("march_ms", "field_ms", "composite_ms")},
+        "roofline": {"kernel": "field (fused warp + residual MLP + hash + canonical MLP)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                     "bytes_per_live_sample": bytes_per_sample,
+                     "traffic": float(traffic) if traffic else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
+                "d2h_bytes_per_step": n_rays * 16},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, poses, a.cpu_pixels)
+    S.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -229,7 +229,8 @@ nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out);
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,
  * [2] compositing (each summed over ray chunks), [3] the number of field
- * launches.  CUDA events on the render's stream bracket every launch; this
+ * launches (ray chunks), [4] the number of live samples the field evaluated.
+ * ms_out holds 5 floats.  CUDA events on the render's stream bracket every launch; this
  * call waits for them.  NR_ESTATE if no profiled render has run. */
 nr_status nr_stage_times(nr_subject *s, float *ms_out);
 

@@ -338,7 +338,8 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   const bool prof = (opts->flags & NR_RENDER_PROFILE) != 0;
   const uint32_t n_chunks = (n_rays + chunk - 1) / chunk;
   if (prof) {
-    NR_REQUIRE(4 * n_chunks <= (uint32_t)nr_subject::kProfEvents, "nr_render: too many ray chunks to profile");
+    NR_REQUIRE(4 * n_chunks <= (uint32_t)nr_subject::kProfEvents && n_chunks <= (uint32_t)kCounters,
+               "nr_render: too many ray chunks to profile");
     for (uint32_t i = 0; i < 4 * n_chunks; ++i)
       if (!s->prof_ev[i]) NR_CHECK_CUDA(cudaEventCreate(&s->prof_ev[i]));
     s->prof_used = 0;
@@ -349,12 +350,13 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
     const uint32_t nr_ = std::min(chunk, n_rays - r0);
     mp.ray0 = r0;
     mp.ray_end = r0 + nr_;
-    NR_CHECK_CUDA(cudaMemsetAsync(s->counter, 0, sizeof(uint32_t), st));
+    uint32_t *cnt = s->counter + (ci % kCounters);
+    NR_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));
     NR_CHECK_CUDA(mark(4 * ci));
-    march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, s->samp, s->ray_range, s->counter);
+    march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, s->samp, s->ray_range, cnt);
     NR_CHECK_CUDA(cudaGetLastError());
     NR_CHECK_CUDA(mark(4 * ci + 1));
-    if ((r = launch_field(P, opts->mlp_dtype, kModeRender, s->samp, 0, s->counter, (float *)s->samp_out, s->device,
+    if ((r = launch_field(P, opts->mlp_dtype, kModeRender, s->samp, 0, cnt, (float *)s->samp_out, s->device,
                           st)) != NR_OK)
       return r;
     NR_CHECK_CUDA(mark(4 * ci + 2));
@@ -388,10 +390,16 @@ extern "C" nr_status nr_stage_times(nr_subject *s, float *ms) {
       NR_CHECK_CUDA(cudaEventElapsedTime(&t, s->prof_ev[4 * c + k], s->prof_ev[4 * c + k + 1]));
       acc[k] += t;
     }
+  uint32_t live[kCounters];
+  const int nc = std::min(s->prof_chunks, kCounters);
+  NR_CHECK_CUDA(cudaMemcpy(live, s->counter, sizeof(uint32_t) * nc, cudaMemcpyDeviceToHost));
+  double total = 0;
+  for (int c = 0; c < nc; ++c) total += live[c];
   ms[0] = acc[0];
   ms[1] = acc[1];
   ms[2] = acc[2];
   ms[3] = (float)s->prof_chunks;
+  ms[4] = (float)total;
   return NR_OK;
 }
 

@@ -10,6 +10,7 @@ namespace nr {
 
 constexpr int kModeRender = 0;   // input float4 (x, y, z, delta), output float4 (r, g, b, alpha)
 constexpr int kModeQuery = 1;    // input float3 points, output NR_QUERY_STRIDE floats per point
+constexpr int kCounters = 16;    // device counters per subject: live samples of each ray chunk
 
 struct CamParams {
   float R[9], t[3];

@@ -25,6 +25,7 @@ NR_GRAD_ONLY = 1
 NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_ALL = 1, 2, 4, 8, 15
 NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES = range(4)
 NR_QUERY_STRIDE = 12
+NR_RENDER_PROFILE = 1
 NR_ABI_VERSION = 1
 
 _fp = C.POINTER(C.c_float)
@@ -82,6 +83,8 @@ def _load() -> C.CDLL:
         "nr_params_changed": ([vp], C.c_int),
         "nr_pose_transforms": ([vp, _fp], C.c_int),
         "nr_occupancy": ([vp, _up], C.c_int),
+        "nr_stage_times": ([vp, _fp], C.c_int),
+        "nr_launch_count": ([], C.c_uint64),
         "nr_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -133,11 +136,24 @@ def make_camera(cam) -> nr_camera:
 
 
 def make_opts(mlp: str = "f32", feat: str = "f32", occupancy: bool = False, t_min: float = 0.0,
-              hann_alpha: float = -1.0) -> nr_render_opts:
+              hann_alpha: float = -1.0, profile: bool = False) -> nr_render_opts:
     o = nr_render_opts()
     o.mlp_dtype, o.feat_dtype = DTYPES[mlp], DTYPES[feat]
-    o.use_occupancy, o.t_min, o.hann_alpha, o.flags = int(bool(occupancy)), float(t_min), float(hann_alpha), 0
+    o.use_occupancy, o.t_min, o.hann_alpha = int(bool(occupancy)), float(t_min), float(hann_alpha)
+    o.flags = NR_RENDER_PROFILE if profile else 0
     return o
+
+
+def nr_stage_times(h) -> dict:
+    """Stage times (ms) and live-sample count of the last profiled nr_render."""
+    ms = np.zeros(5, np.float32)
+    check(lib.nr_stage_times(h, _ptr(ms)), "nr_stage_times")
+    return dict(march_ms=float(ms[0]), field_ms=float(ms[1]), composite_ms=float(ms[2]),
+                chunks=int(ms[3]), live_samples=int(ms[4]))
+
+
+def nr_launch_count() -> int:
+    return int(lib.nr_launch_count())
 
 
 class _DevArray:
@@ -289,6 +305,9 @@ class Subject:
 
     def pose_transforms(self):
         return nr_pose_transforms(self.h)
+
+    def stage_times(self):
+        return nr_stage_times(self.h)
 
     def occupancy(self):
         return nr_occupancy(self.h, self.occ_grid)

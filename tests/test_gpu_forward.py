@@ -167,3 +167,42 @@ def test_ragged_sizes(tiny_structured, res, S):
     got = gpu_render(cfg["subject"], cfg["pose"], cam, False)
     ref = oracle_render(cfg["subject"], cfg["pose"], cam, False).reshape(got.shape)
     assert np.abs(got - ref).max() <= TOL_F32
+
+
+@pytest.mark.parametrize("mlp", ["bf16", "f16"])
+@pytest.mark.parametrize("feat", ["f32", "f16"])
+def test_tensor_core_tiers_psnr(tiny_structured, mlp, feat):
+    """Reduced-precision tiers against the oracle: PSNR >= 50 dB (and reported max-abs)."""
+    cfg = tiny_structured
+    s = dict(cfg["subject"])
+    # f16 storage of the table: the tier reads entries rounded to f16
+    got = gpu_render(s, cfg["pose"], cfg["camera"], False, mlp=mlp, feat=feat)
+    ref = oracle_render(s, cfg["pose"], cfg["camera"], False).reshape(got.shape)
+    p = psnr(got, ref)
+    assert p >= 50.0, (p, float(np.abs(got - ref).max()))
+
+
+@pytest.mark.parametrize("mlp", ["bf16", "f16"])
+def test_tensor_core_tier_frame_field(frame, mlp):
+    cam = _small(frame["camera"], 64)
+    got = gpu_render(frame["subject"], frame["pose"], cam, True, mlp=mlp, feat="f16")
+    ref = oracle_render(frame["subject"], frame["pose"], cam, True).reshape(got.shape)
+    assert psnr(got, ref) >= 50.0
+
+
+def test_tensor_core_query_matches_f32(tiny_structured):
+    """Per-sample outputs of the bf16 tier against the float32 tier on the same points."""
+    nr = nrmod()
+    cfg = tiny_structured
+    x = torch.from_numpy(np.random.default_rng(5).uniform(-0.9, 0.9, size=(1000, 3)).astype(np.float32)).cuda()
+    S = nr.Subject(cfg["subject"])
+    try:
+        S.set_pose(*cfg["pose"])
+        a = S.query(x, nr.make_opts("f32")).cpu().numpy()
+        b = S.query(x, nr.make_opts("bf16")).cpu().numpy()
+    finally:
+        S.close()
+    assert np.array_equal(a[:, :4], b[:, :4])            # the warp is float32 in both tiers
+    m = a[:, 3] > 1e-2
+    assert np.abs(a[m, 4:7] - b[m, 4:7]).max() < 2e-3    # x_final through the bf16 residual MLP
+    assert np.abs(a[m, 8:11] - b[m, 8:11]).max() < 3e-2
