@@ -162,6 +162,28 @@ typedef struct {
 nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_render_opts *opts,
                     float *out_rgba, void *stream);
 
+/* nr_render without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let the library call
+ * cudaMalloc at render time -- a real-time serving thread that must not
+ * stall on the implicit device synchronisation of an allocation, a process
+ * that has already handed all free device memory to its own pool, or code
+ * recording a CUDA stream capture, where allocation is not permitted.
+ * It renders exactly like nr_render, but its work queues live in one
+ * fixed, file-scope device array of 8.5 MiB per device (every GPU that
+ * loads the library holds it until the process exits) instead of buffers
+ * the subject allocates.
+ * Limits: width * height <= 65,536 rays and width * height * n_samples
+ * <= 262,144 sample slots; larger frames return NR_EINVAL with a message
+ * saying which limit was exceeded.  out_rgba must be device memory
+ * (NR_EINVAL otherwise); the subject and its pose must already exist.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and must come before any stream capture.
+ * All calls on a device share the one array and leave the last call's data
+ * in it: calls whose GPU work overlaps (other streams or host threads) race
+ * and corrupt each other's results, so serialise them. */
+nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const nr_render_opts *opts,
+                           float *out_rgba, void *stream);
+
 #define NR_QUERY_STRIDE 12
 /* Evaluates the field at n observation-space points x_obs[n][3] (device) for
  * the current pose and writes out[n][12] (device):

@@ -46,6 +46,11 @@ __device__ __forceinline__ bool clip_box(const float o[3], const float d[3], con
   return !miss && lo < hi;
 }
 
+__global__ void march_kernel(CamParams cam, MarchParams mp, float4 *__restrict__ samp, uint2 *__restrict__ ray_range,
+                             uint32_t *__restrict__ counter);
+__global__ void composite_kernel(const uint2 *__restrict__ ray_range, const float4 *__restrict__ so, uint32_t n_rays,
+                                 float t_min, float bg0, float bg1, float bg2, float4 *__restrict__ out);
+
 CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,

@@ -83,6 +83,7 @@ def _load() -> C.CDLL:
         "nr_params_changed": ([vp], C.c_int),
         "nr_pose_transforms": ([vp, _fp], C.c_int),
         "nr_occupancy": ([vp, _up], C.c_int),
+        "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
         "nr_last_error": ([], C.c_char_p),
@@ -210,6 +211,12 @@ def nr_render(h, cam: nr_camera, opts: nr_render_opts, out, stream=None) -> None
     """out: a CUDA tensor or a host numpy/torch buffer of height*width*4 float32."""
     ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
     check(lib.nr_render(h, C.byref(cam), C.byref(opts), C.c_void_p(ptr), _stream(stream)), "nr_render")
+
+
+def nr_render_static(h, cam: nr_camera, opts: nr_render_opts, out, stream=None) -> None:
+    """Allocation-free render into a CUDA tensor (see include/nr.h for its limits)."""
+    check(lib.nr_render_static(h, C.byref(cam), C.byref(opts), C.c_void_p(out.data_ptr()), _stream(stream)),
+          "nr_render_static")
 
 
 def nr_query(h, x_obs, opts: nr_render_opts, out, stream=None) -> None:
