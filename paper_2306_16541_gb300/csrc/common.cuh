@@ -160,14 +160,31 @@ struct nr_subject {
   cudaEvent_t prof_ev[kProfEvents] = {};
   int prof_used = 0;                 // events recorded by the last profiled render
   int prof_chunks = 0;
-  // training workspace
-  size_t tw_rays = 0;
-  float *t_ray = nullptr;            // [n][8]: rgb_hat, T_final, dL/dC (3), pad
+  // training workspace (grow-only)
+  size_t tw_samples = 0;             // capacity of t_samp / t_out / t_T
+  size_t tw_rays = 0;                // capacity of t_raycnt
+  size_t tw_acc = 0;                 // capacity of t_wacc (floats)
+  size_t tw_red = 0, tw_scratch = 0;  // capacities of t_red, t_scratch (floats)
+  float4 *t_samp = nullptr;          // [n_rays * S] x, y, z, delta
+  float4 *t_out = nullptr;           // [n_rays * S] (r, g, b, alpha), then (dL/dc, dL/dalpha)
+  float *t_T = nullptr;              // [n_rays * S] transmittance before each sample
+  uint32_t *t_raycnt = nullptr;      // [n_rays] S if the ray meets the box, else 0
+  float *t_scratch = nullptr;        // per-thread activation columns of the backward kernel
+  float *t_wacc = nullptr;           // per-warp private MLP-gradient accumulators
+  float *t_red = nullptr;            // their sum (float32 blob layout + per-frame bias rows)
   float *loss_acc = nullptr;         // [1]
-  float *f_dbias1 = nullptr;         // [F][64] gradient of the per-frame first-layer bias
+  float *f_dbias1 = nullptr;         // [F][64] (unused, kept for layout)
 };
 
 namespace nr {
+// Offsets (floats) of each layer's W[out][in] and b[out] in the packed master parameters.
+struct MasterOffsets {
+  int r[5], rb[5];                   // residual MLP layers 1..5
+  int c[kMaxHidden + 2], cb[kMaxHidden + 2];   // canonical MLP layers 0..H
+  int n_res, n_mlp;
+};
+MasterOffsets master_offsets(const nr_subject *s);
+int res_gamma_dims(const nr_subject *s);
 void count_launches(uint64_t n);                              // kernels launched by the library
 bool subject_ok(const nr_subject *s);
 nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs

@@ -46,6 +46,37 @@ __device__ __forceinline__ bool clip_box(const float o[3], const float d[3], con
   return !miss && lo < hi;
 }
 
+// --------------------------------------------------------------- ray setup
+// Ray of pixel (u, v), clipped to [t_near, t_far] and the box (Sec. 4.4:
+// samples lie inside the performer's bounding box).  Every operation is an
+// explicitly rounded float32 operation (no FMA contraction): which rays hit
+// the box and which cell a sample falls in are integer decisions, and they
+// must come out the same on every platform.  Evaluation order:
+//   o_k = -(((R0k t0) + (R1k t1)) + (R2k t2))
+//   a = ((u + 0.5) - cx) / fx, b = ((v + 0.5) - cy) / fy
+//   w_k = ((R0k a) + (R1k b)) + R2k,  n = sqrt(((w0 w0) + (w1 w1)) + (w2 w2)),  d_k = w_k / n
+//   per axis with d_k != 0: ta = (bmin_k - o_k) / d_k, tb = (bmax_k - o_k) / d_k,
+//     lo = max(lo, min(ta, tb)), hi = min(hi, max(ta, tb)); an axis with d_k == 0
+//     misses when o_k lies outside its slab.
+__device__ __forceinline__ void camera_origin(const CamParams &c, float o[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    o[k] = -__fadd_rn(__fadd_rn(__fmul_rn(c.R[k], c.t[0]), __fmul_rn(c.R[3 + k], c.t[1])), __fmul_rn(c.R[6 + k], c.t[2]));
+}
+
+__device__ __forceinline__ bool ray_setup(const CamParams &c, const float o[3], const float bmin[3], const float bmax[3],
+                                          uint32_t u, uint32_t v, float d[3], float &lo, float &hi) {
+  const float a = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
+  const float b = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
+  float w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], a), __fmul_rn(c.R[3 + k], b)), c.R[6 + k]);
+  const float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2])));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = __fdiv_rn(w[k], n);
+  return clip_box(o, d, bmin, bmax, c.t_near, c.t_far, lo, hi);
+}
+
 __global__ void march_kernel(CamParams cam, MarchParams mp, float4 *__restrict__ samp, uint2 *__restrict__ ray_range,
                              uint32_t *__restrict__ counter);
 __global__ void composite_kernel(const uint2 *__restrict__ ray_range, const float4 *__restrict__ so, uint32_t n_rays,

@@ -211,16 +211,9 @@ __global__ void fold_pose_bias_kernel(const float *__restrict__ res, int g, int 
   bias1[f * kWidth + j] = acc;
 }
 
-static int res_gamma_dims(const nr_subject *s) { return 3 + 6 * (int)s->res_freqs; }
+int res_gamma_dims(const nr_subject *s) { return 3 + 6 * (int)s->res_freqs; }
 
-// Offsets of the packed master parameters.
-struct MasterOffsets {
-  int r[5], rb[5];        // residual W_l, b_l
-  int c[kMaxHidden + 2], cb[kMaxHidden + 2];
-  int n_res, n_mlp;
-};
-
-static MasterOffsets master_offsets(const nr_subject *s) {
+MasterOffsets master_offsets(const nr_subject *s) {
   MasterOffsets m{};
   const int g = res_gamma_dims(s), P = 3 * (int)s->K;
   const int rin[5] = {g + P, kWidth, kWidth, kWidth + g, kWidth};
@@ -452,7 +445,8 @@ static void free_subject(nr_subject *s) {
                   s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->blob,      s->tc_bf16,   s->tc_f16,
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
-                  s->t_ray,  s->loss_acc, s->f_dbias1};
+                  s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
+                  s->loss_acc, s->f_dbias1};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
@@ -506,7 +500,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   s->width = d->mlp_width;
   s->hidden = d->mlp_hidden_layers;
   s->res_enabled = d->res_enabled;
-  s->res_freqs = d->res_enabled ? d->res_pe_freqs : 0;
+  s->res_freqs = d->res_pe_freqs;
   s->occ_grid = d->occ_grid ? d->occ_grid : 128;
   s->has_ellipsoids = d->ellipsoids != nullptr;
   s->parents.assign(d->parents, d->parents + s->K);

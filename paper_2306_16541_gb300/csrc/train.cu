@@ -1,12 +1,780 @@
-// train.cu -- training step: forward with saved per-ray state, the
-// hand-written backward and Adam.
+// train.cu -- one training step (Sec. 5.2): stratified samples of a batch of
+// pixel rays, the float32 field forward, compositing with the squared-error
+// loss, the hand-written backward (compositing adjoint, canonical MLP, hash
+// scatter-add, residual MLP through the positional encoding, inverse-LBS
+// scatter-add into the weight volume) and Adam.
+//
+// Gradient accumulation without contention:
+//   * hash-table and weight-volume gradients are scattered with float2 /
+//     float atomics straight into the gradient buffers;
+//   * MLP weight gradients dW = sum_s delta_s (x) h_s are reduced per warp:
+//     after a tile of 32 samples, every lane owns two output rows of a layer
+//     and sums the 32 samples' products for them, then adds the result into
+//     that warp's private accumulator (plain read-modify-write, no atomics);
+//     one reduction kernel sums the private accumulators at the end.
+//   * each thread keeps its forward activations and backward deltas in its
+//     own column of an L2-resident scratch buffer, which the warp reads back
+//     in the reduction.
+#include <math.h>
+#include <string.h>
+
 #include "field.cuh"
 #include "render.cuh"
+
+namespace nr {
+
+constexpr int kBwdThreads = 128;
+constexpr int kBwdWarps = kBwdThreads / 32;
+
+// Rows of a thread's scratch column.
+constexpr int R_GAM = 0;                        // gamma(x_skel)            48
+constexpr int R_RH = R_GAM + kResGammaPad;      // residual h1..h4          4 x 64
+constexpr int R_ENC = R_RH + 4 * kWidth;        // hash encoding            32
+constexpr int R_CH = R_ENC + kMlpIn;            // canonical h1..hH         4 x 64
+constexpr int D_C = R_CH + kMaxHidden * kWidth; // canonical deltas h1..hH  4 x 64, then output 4
+constexpr int D_CL_MAX = D_C + kMaxHidden * kWidth;
+constexpr int D_R = D_CL_MAX + 4;               // residual deltas h1..h4   4 x 64, then output 4
+constexpr int D_R5 = D_R + 4 * kWidth;
+constexpr int R_DENC = D_R5 + 4;                // dL/d encoding            32
+constexpr int R_DGAM = R_DENC + kMlpIn;         // dL/d gamma               48
+constexpr int kRows = R_DGAM + kResGammaPad;
+
+struct TrainDev {
+  const uint32_t *frame_id, *px, *py;
+  const float *target;
+  uint32_t n_rays, S;
+  uint64_t seed;
+  float bg[3];
+  const Frame *cams;
+  const float *fG, *fbias1, *fomega;
+  float4 *samp, *out;
+  float *T;
+  uint32_t *raycnt;
+  float *loss;
+  float2 *g_table;
+  float *g_wvol;
+  float *scratch, *wacc;
+  int acc_floats;         // floats per warp accumulator
+  int n_frames;
+};
+
+// ----------------------------------------------------------------- rays
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  // SplitMix64 (Steele, Lea and Flood 2014): output k of the generator seeded with `seed`
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// One thread per (ray, bin): stratified sample t_i = lo + (i + u_i) D inside the
+// clipped ray, delta_i = t_{i+1} - t_i, delta_{S-1} = hi - t_{S-1}.
+__global__ void __launch_bounds__(256) train_samples_kernel(TrainDev T, float bx, float by, float bz, float Bx,
+                                                            float By, float Bz) {
+  const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= (uint64_t)T.n_rays * T.S) return;
+  const uint32_t r = (uint32_t)(q / T.S), i = (uint32_t)(q % T.S);
+  const Frame &F = T.cams[T.frame_id[r]];
+  CamParams c;
+  for (int k = 0; k < 9; ++k) c.R[k] = F.R[k];
+  for (int k = 0; k < 3; ++k) c.t[k] = F.t[k];
+  c.fx = F.fx; c.fy = F.fy; c.cx = F.cx; c.cy = F.cy; c.t_near = F.t_near; c.t_far = F.t_far;
+  const float bmin[3] = {bx, by, bz}, bmax[3] = {Bx, By, Bz};
+  float o[3], d[3], lo, hi;
+  camera_origin(c, o);
+  const bool hit = ray_setup(c, o, bmin, bmax, T.px[r], T.py[r], d, lo, hi);
+  if (i == 0) T.raycnt[r] = hit ? T.S : 0u;
+  if (!hit) {
+    T.samp[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float D = (hi - lo) / (float)T.S;
+  auto u_of = [&](uint32_t ii) {
+    const uint64_t z = splitmix64(T.seed, (uint64_t)r * T.S + ii + 1);
+    return (float)(z >> 40) * (1.0f / 16777216.0f);
+  };
+  const float t = lo + ((float)i + u_of(i)) * D;
+  const float tn = (i + 1 < T.S) ? lo + ((float)(i + 1) + u_of(i + 1)) * D : hi;
+  T.samp[q] = make_float4(o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2], tn - t);
+}
+
+// ------------------------------------------------------------ forward field
+// The float32 field of render.cu, with the pose of each sample's frame.
+__global__ void __launch_bounds__(192, 1) train_fwd_kernel(FieldParams P, TrainDev T) {
+  extern __shared__ float4 smem4[];
+  float *sW = reinterpret_cast<float *>(smem4);
+  float *sCol = sW + P.lay.total;
+  for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
+    reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
+  __syncthreads();
+  const int stride = blockDim.x;
+  float *hcol = sCol + threadIdx.x;
+  float *gcol = hcol + kWidth * stride;
+  const uint32_t n = T.n_rays * T.S;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t r = j / T.S;
+    if (!T.raycnt[r]) {
+      T.out[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const uint32_t f = T.frame_id[r];
+    const float *G = T.fG + (size_t)f * kBones * 12;
+    const float4 s = T.samp[j];
+    float s0, s1, s2, S;
+    lbs_warp(P, G, s.x, s.y, s.z, s0, s1, s2, S);
+    float f0 = s0, f1 = s1, f2 = s2;
+    if (P.res_enabled) {
+      pos_enc(P, s0, s1, s2, gcol, stride);
+      float r0, r1, r2;
+      residual_f32(P, sW, T.fbias1 + (size_t)f * kWidth, gcol, hcol, stride, r0, r1, r2);
+      f0 += r0;
+      f1 += r1;
+      f2 += r2;
+    }
+    const bool inside = hash_encode(P, f0, f1, f2, hcol, stride);
+    float o[4];
+    canonical_f32(P, sW, hcol, stride, o);
+    const float a = inside ? (1.f - expf(-softplusf_(o[3]) * s.w)) * fminf(S, 1.f) : 0.f;
+    T.out[j] = make_float4(sigmoidf_(o[0]), sigmoidf_(o[1]), sigmoidf_(o[2]), a);
+  }
+}
+
+// ------------------------------------------------- compositing and its adjoint
+// Per ray: C = sum_i T_i alpha_i c_i + T_S bg, T_{i+1} = T_i (1 - alpha_i) (Eq. 3),
+// loss term sum_k (C_k - C_gt,k)^2 / (3 N), g = dL/dC.  The reverse scan keeps
+// B_i = sum_{j>i} alpha_j prod_{i<k<j}(1 - alpha_k) (c_j . g) + prod_{k>i}(1 - alpha_k) (bg . g)
+// (B_{S-1} = bg . g, B_{i-1} = alpha_i (c_i . g) + (1 - alpha_i) B_i) so that
+//   dL/dc_i = T_i alpha_i g,  dL/dalpha_i = T_i (c_i . g - B_i)
+// without dividing by (1 - alpha_i).
+__global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  float lsum = 0.f;
+  if (r < T.n_rays) {
+    const size_t base = (size_t)r * T.S;
+    const uint32_t cnt = T.raycnt[r];
+    float Tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    for (uint32_t i = 0; i < cnt; ++i) {
+      const float4 v = T.out[base + i];
+      T.T[base + i] = Tr;
+      const float w = Tr * v.w;
+      c0 = fmaf(w, v.x, c0);
+      c1 = fmaf(w, v.y, c1);
+      c2 = fmaf(w, v.z, c2);
+      Tr *= 1.f - v.w;
+    }
+    const float C0 = fmaf(Tr, T.bg[0], c0), C1 = fmaf(Tr, T.bg[1], c1), C2 = fmaf(Tr, T.bg[2], c2);
+    const float e0 = C0 - T.target[3 * r], e1 = C1 - T.target[3 * r + 1], e2 = C2 - T.target[3 * r + 2];
+    lsum = e0 * e0 + e1 * e1 + e2 * e2;
+    const float scale = 2.f / (3.f * (float)T.n_rays);
+    const float g0 = scale * e0, g1 = scale * e1, g2 = scale * e2;
+    float B = T.bg[0] * g0 + T.bg[1] * g1 + T.bg[2] * g2;
+    for (int i = (int)cnt - 1; i >= 0; --i) {
+      const float4 v = T.out[base + i];
+      const float Ti = T.T[base + i];
+      const float cg = v.x * g0 + v.y * g1 + v.z * g2;
+      const float ta = Ti * v.w;
+      T.out[base + i] = make_float4(ta * g0, ta * g1, ta * g2, Ti * (cg - B));
+      B = fmaf(v.w, cg, (1.f - v.w) * B);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(T.loss, lsum / (3.f * (float)T.n_rays));
+}
+
+// ---------------------------------------------------------------- backward
+// delta_prev[k] = (sum_j Wt[k][j] delta[j]) * (h_prev[k] > 0), Wt = W^T ([in][OUT]).
+template <int OUT>
+__device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const float *dcol, int in, const float *hcol,
+                                           float *outcol, int stride) {
+  float d[OUT];
+#pragma unroll
+  for (int j = 0; j < OUT; ++j) d[j] = dcol[j * stride];
+#pragma unroll 2
+  for (int k = 0; k < in; ++k) {
+    const float4 *row = reinterpret_cast<const float4 *>(Wt + k * OUT);
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < OUT / 4; ++j) {
+      const float4 w = row[j];
+      acc = fmaf(w.x, d[4 * j], fmaf(w.y, d[4 * j + 1], fmaf(w.z, d[4 * j + 2], fmaf(w.w, d[4 * j + 3], acc))));
+    }
+    if (hcol) acc = hcol[k * stride] > 0.f ? acc : 0.f;
+    outcol[k * stride] = acc;
+  }
+}
+
+// Warp-level weight gradient of one layer with 64 outputs: acc[wt + k*64 + j] += sum_s h[s][k] d[s][j],
+// acc[b + j] += sum_s d[s][j]; lane owns j = lane and lane + 32.  `wcol` points at the warp's
+// column 0 (so row r of sample s is wcol[r * stride + s]).
+__device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in, int n_in, int r_d, float *acc,
+                                        int wt, int b, bool with_bias) {
+  const int lane = threadIdx.x & 31;
+  float d0[32], d1[32];
+  const float4 *p0 = reinterpret_cast<const float4 *>(wcol + (r_d + lane) * stride);
+  const float4 *p1 = reinterpret_cast<const float4 *>(wcol + (r_d + lane + 32) * stride);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = p0[q], c = p1[q];
+    d0[4 * q] = a.x; d0[4 * q + 1] = a.y; d0[4 * q + 2] = a.z; d0[4 * q + 3] = a.w;
+    d1[4 * q] = c.x; d1[4 * q + 1] = c.y; d1[4 * q + 2] = c.z; d1[4 * q + 3] = c.w;
+  }
+  if (with_bias) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+      s0 += d0[s];
+      s1 += d1[s];
+    }
+    acc[b + lane] += s0;
+    acc[b + lane + 32] += s1;
+  }
+  for (int k = 0; k < n_in; ++k) {
+    const float4 *ph = reinterpret_cast<const float4 *>(wcol + (r_in + k) * stride);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 h = ph[q];
+      a0 = fmaf(h.x, d0[4 * q], fmaf(h.y, d0[4 * q + 1], fmaf(h.z, d0[4 * q + 2], fmaf(h.w, d0[4 * q + 3], a0))));
+      a1 = fmaf(h.x, d1[4 * q], fmaf(h.y, d1[4 * q + 1], fmaf(h.z, d1[4 * q + 2], fmaf(h.w, d1[4 * q + 3], a1))));
+    }
+    acc[wt + k * kWidth + lane] += a0;
+    acc[wt + k * kWidth + lane + 32] += a1;
+  }
+}
+
+// Same for a layer with 4 (padded) outputs and 64 inputs: lane owns input rows k = lane, lane + 32.
+__device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, int r_d, int n_out, float *acc, int wt,
+                                       int b) {
+  const int lane = threadIdx.x & 31;
+  float h0[32], h1[32];
+  const float4 *p0 = reinterpret_cast<const float4 *>(wcol + (r_in + lane) * stride);
+  const float4 *p1 = reinterpret_cast<const float4 *>(wcol + (r_in + lane + 32) * stride);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = p0[q], c = p1[q];
+    h0[4 * q] = a.x; h0[4 * q + 1] = a.y; h0[4 * q + 2] = a.z; h0[4 * q + 3] = a.w;
+    h1[4 * q] = c.x; h1[4 * q + 1] = c.y; h1[4 * q + 2] = c.z; h1[4 * q + 3] = c.w;
+  }
+  for (int j = 0; j < n_out; ++j) {
+    const float4 *pd = reinterpret_cast<const float4 *>(wcol + (r_d + j) * stride);
+    float a0 = 0.f, a1 = 0.f, sb = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 d = pd[q];
+      a0 = fmaf(h0[4 * q], d.x, fmaf(h0[4 * q + 1], d.y, fmaf(h0[4 * q + 2], d.z, fmaf(h0[4 * q + 3], d.w, a0))));
+      a1 = fmaf(h1[4 * q], d.x, fmaf(h1[4 * q + 1], d.y, fmaf(h1[4 * q + 2], d.z, fmaf(h1[4 * q + 3], d.w, a1))));
+      sb += d.x + d.y + d.z + d.w;
+    }
+    acc[wt + lane * 4 + j] += a0;
+    acc[wt + (lane + 32) * 4 + j] += a1;
+    if (lane == 0) acc[b + j] += sb;
+  }
+}
+
+// One thread per sample: forward recompute (activations into the thread's scratch
+// column), backward, scatter-adds, then the warp's weight-gradient reduction.
+__global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P, TrainDev T) {
+  extern __shared__ float4 smem4[];
+  float *sW = reinterpret_cast<float *>(smem4);
+  for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
+    reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
+  __syncthreads();
+  const BlobLayout &Ly = P.lay;
+  const int stride = blockDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *colbase = T.scratch + (size_t)blockIdx.x * kRows * stride;
+  float *col = colbase + threadIdx.x;                  // this thread's column
+  const float *wcol = colbase + warp * 32;             // the warp's column 0
+  float *acc = T.wacc + ((size_t)blockIdx.x * kBwdWarps + warp) * T.acc_floats;
+  float *accF = acc + Ly.total;                        // per-frame first-layer bias gradients [F][64]
+  const int H = P.hidden;
+  const uint32_t n = T.n_rays * T.S;
+  const uint32_t step = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (n + step - 1) / step;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t j = it * step + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t r = j < n ? j / T.S : 0;
+    bool active = j < n && T.raycnt[r] != 0;
+    const uint32_t f = active ? T.frame_id[r] : 0;
+    float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) g4 = T.out[j];
+    if (active) {
+      // ---------------- forward recompute
+      const float *G = T.fG + (size_t)f * kBones * 12;
+      const float4 s = T.samp[j];
+      float xs0, xs1, xs2, S;
+      lbs_warp(P, G, s.x, s.y, s.z, xs0, xs1, xs2, S);
+      float xf0 = xs0, xf1 = xs1, xf2 = xs2;
+      float y[kWidth];
+      const float *bias1 = T.fbias1 + (size_t)f * kWidth;
+      pos_enc(P, xs0, xs1, xs2, col + R_GAM * stride, stride);
+      if (P.res_enabled) {
+        dense_f32<kWidth>(sW + Ly.r1, bias1, col + R_GAM * stride, kResGammaPad, stride, y);
+        store_relu(y, col + (R_RH + 0 * kWidth) * stride, stride);
+        dense_f32<kWidth>(sW + Ly.r2, sW + Ly.r2b, col + (R_RH + 0 * kWidth) * stride, kWidth, stride, y);
+        store_relu(y, col + (R_RH + 1 * kWidth) * stride, stride);
+        dense_f32<kWidth>(sW + Ly.r3, sW + Ly.r3b, col + (R_RH + 1 * kWidth) * stride, kWidth, stride, y);
+        store_relu(y, col + (R_RH + 2 * kWidth) * stride, stride);
+        dense_f32<kWidth>(sW + Ly.r4, sW + Ly.r4b, col + (R_RH + 2 * kWidth) * stride, kWidth, stride, y);
+        dense_acc_f32<kWidth>(sW + Ly.r4 + kWidth * kWidth, col + R_GAM * stride, kResGammaPad, stride, y);
+        store_relu(y, col + (R_RH + 3 * kWidth) * stride, stride);
+        float o3[4];
+        dense_f32<4>(sW + Ly.r5, sW + Ly.r5b, col + (R_RH + 3 * kWidth) * stride, kWidth, stride, o3);
+        xf0 += o3[0];
+        xf1 += o3[1];
+        xf2 += o3[2];
+      } else {
+        for (int q = 0; q < 4 * kWidth; ++q) col[(R_RH + q) * stride] = 0.f;
+      }
+      const bool inside = hash_encode(P, xf0, xf1, xf2, col + R_ENC * stride, stride);
+      dense_f32<kWidth>(sW + Ly.c0, sW + Ly.c0b, col + R_ENC * stride, kMlpIn, stride, y);
+      store_relu(y, col + R_CH * stride, stride);
+      for (int l = 1; l < H; ++l) {
+        dense_f32<kWidth>(sW + Ly.ch[l - 1], sW + Ly.chb[l - 1], col + (R_CH + (l - 1) * kWidth) * stride, kWidth,
+                          stride, y);
+        store_relu(y, col + (R_CH + l * kWidth) * stride, stride);
+      }
+      float o[4];
+      dense_f32<4>(sW + Ly.cl, sW + Ly.clb, col + (R_CH + (H - 1) * kWidth) * stride, kWidth, stride, o);
+      active = inside;
+      if (active) {
+        // ---------------- alpha, rgb, sigma
+        const float sig = softplusf_(o[3]);
+        const float e = expf(-sig * s.w);
+        const float lk = fminf(S, 1.f);
+        const float dsig = g4.w * s.w * e * lk;
+        const float dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
+        const float gc[3] = {g4.x, g4.y, g4.z};
+        float* dcl = col + (D_C + H * kWidth) * stride;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float c = sigmoidf_(o[k]);
+          dcl[k * stride] = gc[k] * c * (1.f - c);
+        }
+        dcl[3 * stride] = dsig * sigmoidf_(o[3]);
+        // ---------------- canonical MLP backward
+        back_layer<4>(sW + Ly.cl, dcl, kWidth, col + (R_CH + (H - 1) * kWidth) * stride,
+                      col + (D_C + (H - 1) * kWidth) * stride, stride);
+        for (int l = H - 1; l >= 1; --l)
+          back_layer<kWidth>(sW + Ly.ch[l - 1], col + (D_C + l * kWidth) * stride, kWidth,
+                             col + (R_CH + (l - 1) * kWidth) * stride, col + (D_C + (l - 1) * kWidth) * stride,
+                             stride);
+        back_layer<kWidth>(sW + Ly.c0, col + D_C * stride, kMlpIn, nullptr, col + R_DENC * stride, stride);
+        // ---------------- hash backward: scatter-add and dL/dx_final
+        float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
+        {
+          const float p0 = (xf0 - P.bmin[0]) * P.inv_box[0];
+          const float p1 = (xf1 - P.bmin[1]) * P.inv_box[1];
+          const float p2 = (xf2 - P.bmin[2]) * P.inv_box[2];
+          for (int l = 0; l < P.L; ++l) {
+            const float da = col[(R_DENC + 2 * l) * stride], db = col[(R_DENC + 2 * l + 1) * stride];
+            const uint32_t N = P.level_res[l];
+            const float fn = (float)N;
+            const float q0 = p0 * fn, q1 = p1 * fn, q2 = p2 * fn;
+            const float a0 = fminf(floorf(q0), fn - 1.f), a1 = fminf(floorf(q1), fn - 1.f),
+                        a2 = fminf(floorf(q2), fn - 1.f);
+            const float fr[3] = {q0 - a0, q1 - a1, q2 - a2};
+            HashCell c;
+            hash_cell(P, l, p0, p1, p2, c);
+            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const size_t off = (size_t)l * (P.T_mask + 1) + c.idx[k];
+              atomicAdd(T.g_table + off, make_float2(c.w[k] * da, c.w[k] * db));
+              const float2 v = __ldg(P.table32 + off);
+              const float sv = v.x * da + v.y * db;
+              const float wx = (k & 1) ? fr[0] : 1.f - fr[0], wy = ((k >> 1) & 1) ? fr[1] : 1.f - fr[1],
+                          wz = (k >> 2) ? fr[2] : 1.f - fr[2];
+              const float sx = (k & 1) ? 1.f : -1.f, sy = ((k >> 1) & 1) ? 1.f : -1.f, sz = (k >> 2) ? 1.f : -1.f;
+              gp0 = fmaf(sv, sx * wy * wz, gp0);
+              gp1 = fmaf(sv, wx * sy * wz, gp1);
+              gp2 = fmaf(sv, wx * wy * sz, gp2);
+            }
+            dx0 = fmaf(gp0, fn, dx0);
+            dx1 = fmaf(gp1, fn, dx1);
+            dx2 = fmaf(gp2, fn, dx2);
+          }
+          dx0 *= P.inv_box[0];
+          dx1 *= P.inv_box[1];
+          dx2 *= P.inv_box[2];
+        }
+        // ---------------- residual MLP backward (x_final = x_skel + x_res)
+        float ds0 = dx0, ds1 = dx1, ds2 = dx2;
+        if (P.res_enabled) {
+          float *dr5 = col + D_R5 * stride;
+          dr5[0] = dx0;
+          dr5[stride] = dx1;
+          dr5[2 * stride] = dx2;
+          dr5[3 * stride] = 0.f;
+          back_layer<4>(sW + Ly.r5, dr5, kWidth, col + (R_RH + 3 * kWidth) * stride, col + (D_R + 3 * kWidth) * stride,
+                        stride);
+          back_layer<kWidth>(sW + Ly.r4, col + (D_R + 3 * kWidth) * stride, kWidth, col + (R_RH + 2 * kWidth) * stride,
+                             col + (D_R + 2 * kWidth) * stride, stride);
+          back_layer<kWidth>(sW + Ly.r4 + kWidth * kWidth, col + (D_R + 3 * kWidth) * stride, kResGammaPad, nullptr,
+                             col + R_DGAM * stride, stride);
+          back_layer<kWidth>(sW + Ly.r3, col + (D_R + 2 * kWidth) * stride, kWidth, col + (R_RH + 1 * kWidth) * stride,
+                             col + (D_R + 1 * kWidth) * stride, stride);
+          back_layer<kWidth>(sW + Ly.r2, col + (D_R + 1 * kWidth) * stride, kWidth, col + (R_RH + 0 * kWidth) * stride,
+                             col + (D_R + 0 * kWidth) * stride, stride);
+          {  // dL/dgamma += W1_gamma^T delta1
+            float d[kWidth];
+#pragma unroll
+            for (int q = 0; q < kWidth; ++q) d[q] = col[(D_R + q) * stride];
+            for (int k = 0; k < kResGammaPad; ++k) {
+              const float4 *row = reinterpret_cast<const float4 *>(sW + Ly.r1 + k * kWidth);
+              float a = 0.f;
+#pragma unroll
+              for (int q = 0; q < kWidth / 4; ++q) {
+                const float4 w = row[q];
+                a = fmaf(w.x, d[4 * q], fmaf(w.y, d[4 * q + 1], fmaf(w.z, d[4 * q + 2], fmaf(w.w, d[4 * q + 3], a))));
+              }
+              col[(R_DGAM + k) * stride] += a;
+            }
+          }
+          // through gamma: d gamma / d x_skel
+          const float *dg = col + R_DGAM * stride;
+          const float xh[3] = {(xs0 - P.box_c[0]) * P.box_ih[0], (xs1 - P.box_c[1]) * P.box_ih[1],
+                               (xs2 - P.box_c[2]) * P.box_ih[2]};
+          float dh[3] = {dg[0], dg[stride], dg[2 * stride]};
+          for (int k = 0; k < P.res_freqs; ++k) {
+            const float sc = (float)(1 << k);
+            const float wk = P.hann[k] * sc * 3.14159265358979f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              float sn, cs;
+              sincospif(sc * xh[a], &sn, &cs);
+              dh[a] += wk * (dg[(3 + 6 * k + a) * stride] * cs - dg[(6 + 6 * k + a) * stride] * sn);
+            }
+          }
+          ds0 += dh[0] * P.box_ih[0];
+          ds1 += dh[1] * P.box_ih[1];
+          ds2 += dh[2] * P.box_ih[2];
+        }
+        // ---------------- inverse-LBS backward: scatter into the weight volume
+        {
+          const float D = fmaxf(S, kEpsW);
+          const float m = S > kEpsW ? 1.f : 0.f;
+          const int R = P.wres, R3 = R * R * R;
+          for (int i = 0; i < kBones; ++i) {
+            const float *g = G + 12 * i;
+            const float p0 = fmaf(g[0], s.x, fmaf(g[1], s.y, fmaf(g[2], s.z, g[3])));
+            const float p1 = fmaf(g[4], s.x, fmaf(g[5], s.y, fmaf(g[6], s.z, g[7])));
+            const float p2 = fmaf(g[8], s.x, fmaf(g[9], s.y, fmaf(g[10], s.z, g[11])));
+            const float dw = (ds0 * (p0 - m * xs0) + ds1 * (p1 - m * xs1) + ds2 * (p2 - m * xs2)) / D + dS_alpha;
+            if (dw == 0.f) continue;
+            const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
+            const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
+            const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
+            const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
+            const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+            if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) continue;
+            const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
+            float *chg = T.g_wvol + (size_t)i * R3;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const int ax = ix + (c & 1), ay = iy + ((c >> 1) & 1), az = iz + (c >> 2);
+              if (ax < 0 || ay < 0 || az < 0 || ax >= R || ay >= R || az >= R) continue;
+              const float w = ((c & 1) ? fx : 1.f - fx) * (((c >> 1) & 1) ? fy : 1.f - fy) * ((c >> 2) ? fz : 1.f - fz);
+              atomicAdd(chg + (az * R + ay) * R + ax, dw * w);
+            }
+          }
+        }
+      }
+    }
+    if (!active) {  // contributes nothing: zero every row the warp reduction reads
+      for (int q = 0; q < kRows; ++q) col[q * stride] = 0.f;
+    } else if (!P.res_enabled) {
+      for (int q = D_R; q < D_R5 + 4; ++q) col[q * stride] = 0.f;
+    }
+    __syncwarp();
+    // ---------------- warp-level weight gradients (private accumulator)
+    wgrad64(wcol, stride, R_ENC, kMlpIn, D_C, acc, Ly.c0, Ly.c0b, true);
+    for (int l = 1; l < H; ++l)
+      wgrad64(wcol, stride, R_CH + (l - 1) * kWidth, kWidth, D_C + l * kWidth, acc, Ly.ch[l - 1], Ly.chb[l - 1], true);
+    wgrad4(wcol, stride, R_CH + (H - 1) * kWidth, D_C + H * kWidth, 4, acc, Ly.cl, Ly.clb);
+    if (P.res_enabled) {
+      wgrad64(wcol, stride, R_GAM, kResGammaPad, D_R, acc, Ly.r1, Ly.r1b, true);
+      wgrad64(wcol, stride, R_RH + 0 * kWidth, kWidth, D_R + 1 * kWidth, acc, Ly.r2, Ly.r2b, true);
+      wgrad64(wcol, stride, R_RH + 1 * kWidth, kWidth, D_R + 2 * kWidth, acc, Ly.r3, Ly.r3b, true);
+      wgrad64(wcol, stride, R_RH + 2 * kWidth, kWidth, D_R + 3 * kWidth, acc, Ly.r4, Ly.r4b, true);
+      wgrad64(wcol, stride, R_GAM, kResGammaPad, D_R + 3 * kWidth, acc, Ly.r4 + kWidth * kWidth, 0, false);
+      wgrad4(wcol, stride, R_RH + 3 * kWidth, D_R5, 3, acc, Ly.r5, Ly.r5b);
+      // per-frame sums of delta1 (for W_Omega): lane owns rows lane, lane + 32
+      const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
+      const float *d0 = wcol + (D_R + lane) * stride, *d1 = wcol + (D_R + lane + 32) * stride;
+      int cur = -1;
+      float s0 = 0.f, s1 = 0.f;
+      for (int sI = 0; sI < 32; ++sI) {
+        const uint32_t jj = j0 + sI;
+        if (jj >= n) break;
+        const int fr = (int)T.frame_id[jj / T.S];
+        if (fr != cur) {
+          if (cur >= 0) {
+            accF[cur * kWidth + lane] += s0;
+            accF[cur * kWidth + lane + 32] += s1;
+          }
+          cur = fr;
+          s0 = s1 = 0.f;
+        }
+        s0 += d0[sI];
+        s1 += d1[sI];
+      }
+      if (cur >= 0) {
+        accF[cur * kWidth + lane] += s0;
+        accF[cur * kWidth + lane + 32] += s1;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Sum of the per-warp accumulators: red[e] = sum_w wacc[w][e].
+__global__ void reduce_acc_kernel(const float *__restrict__ wacc, int n_warps, int A, float *__restrict__ red) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A) return;
+  float s = 0.f;
+  for (int w = 0; w < n_warps; ++w) s += wacc[(size_t)w * A + e];
+  red[e] = s;
+}
+
+// Gradients in the packed master layout (W[out][in], b) from the transposed
+// blob-shaped sums; the joint-angle columns of the residual first layer get
+// dL/dW_Omega[j][m] = sum_f (sum of delta1 over frame f)[j] * Omega_f[m].
+struct ScatterArgs {
+  MasterOffsets m;
+  BlobLayout b;
+  int g, pose_dim, n_frames, hidden, mlp_in;
+};
+
+__global__ void scatter_res_kernel(const float *__restrict__ red, const float *__restrict__ fomega, ScatterArgs a,
+                                   float *__restrict__ g_res) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.m.n_res) return;
+  const float *accF = red + a.b.total;
+  // find the layer
+  const int rin[5] = {a.g + a.pose_dim, kWidth, kWidth, kWidth + a.g, kWidth};
+  const int rout[5] = {kWidth, kWidth, kWidth, kWidth, 3};
+  const int wt[5] = {a.b.r1, a.b.r2, a.b.r3, a.b.r4, a.b.r5};
+  const int bb[5] = {a.b.r1b, a.b.r2b, a.b.r3b, a.b.r4b, a.b.r5b};
+  const int ostride[5] = {kWidth, kWidth, kWidth, kWidth, 4};
+  for (int l = 0; l < 5; ++l) {
+    if (e >= a.m.r[l] && e < a.m.rb[l]) {
+      const int q = e - a.m.r[l], j = q / rin[l], k = q % rin[l];
+      float v;
+      if (l == 0 && k >= a.g) {
+        const int mm = k - a.g;
+        v = 0.f;
+        for (int f = 0; f < a.n_frames; ++f) v = fmaf(accF[f * kWidth + j], fomega[f * a.pose_dim + mm], v);
+      } else if (l == 3 && k >= kWidth) {
+        v = red[wt[l] + (kWidth + (k - kWidth)) * ostride[l] + j];
+      } else {
+        v = red[wt[l] + k * ostride[l] + j];
+      }
+      g_res[e] = v;
+      return;
+    }
+    if (e >= a.m.rb[l] && e < a.m.rb[l] + rout[l]) {
+      g_res[e] = red[bb[l] + (e - a.m.rb[l])];
+      return;
+    }
+  }
+}
+
+__global__ void scatter_mlp_kernel(const float *__restrict__ red, ScatterArgs a, float *__restrict__ g_mlp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.m.n_mlp) return;
+  const int H = a.hidden;
+  for (int l = 0; l <= H; ++l) {
+    const int in = l == 0 ? a.mlp_in : kWidth;
+    const int out = l == H ? 4 : kWidth;
+    const int wt = l == 0 ? a.b.c0 : (l == H ? a.b.cl : a.b.ch[l - 1]);
+    const int bb = l == 0 ? a.b.c0b : (l == H ? a.b.clb : a.b.chb[l - 1]);
+    const int ostride = l == H ? 4 : kWidth;
+    if (e >= a.m.c[l] && e < a.m.cb[l]) {
+      const int q = e - a.m.c[l], j = q / in, k = q % in;
+      g_mlp[e] = red[wt + k * ostride + j];
+      return;
+    }
+    if (e >= a.m.cb[l] && e < a.m.cb[l] + out) {
+      g_mlp[e] = red[bb + (e - a.m.cb[l])];
+      return;
+    }
+  }
+}
+
+// Adam with bias correction (Kingma and Ba 2015; Sec. 5.2 uses beta = (0.9, 0.99)):
+// m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, p -= lr (m c1) / (sqrt(v c2) + eps),
+// c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t).  Every entry is updated.
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+template <typename P_>
+static nr_status grow(P_ *&ptr, size_t &cap, size_t need) {
+  if (need <= cap) return NR_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  NR_CHECK_CUDA(cudaMalloc((void **)&ptr, need * sizeof(P_)));
+  cap = need;
+  return NR_OK;
+}
+
+}  // namespace nr
 
 using namespace nr;
 
 extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float *loss_out, void *stream) {
-  (void)s; (void)b; (void)loss_out; (void)stream;
-  set_error("nr_train_step is not implemented yet");
-  return NR_EUNSUPPORTED;
+  NR_REQUIRE(subject_ok(s), "nr_train_step: invalid handle");
+  NR_REQUIRE(b, "nr_train_step: NULL batch");
+  NR_REQUIRE(b->n_rays >= 1 && b->frame_id && b->px && b->py && b->target_rgb, "nr_train_step: empty or NULL batch");
+  NR_REQUIRE(b->n_samples >= 1 && b->n_samples <= 1024, "nr_train_step: n_samples must be 1..1024");
+  NR_REQUIRE((uint64_t)b->n_rays * b->n_samples <= (1ull << 31), "nr_train_step: batch too large");
+  NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
+             "nr_train_step: bad Adam hyper-parameters");
+  if (s->n_frames == 0) {
+    set_error("nr_train_step: call nr_set_frames first");
+    return NR_ESTATE;
+  }
+  NR_CHECK_CUDA(cudaSetDevice(s->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  nr_status r;
+  if ((r = prepare_params(s, st)) != NR_OK) return r;
+  if ((r = fold_frame_biases(s, st)) != NR_OK) return r;
+  nr_render_opts o{};
+  o.mlp_dtype = NR_F32;
+  o.feat_dtype = NR_F32;
+  o.hann_alpha = b->hann_alpha;
+  FieldParams P = field_params(s, &o);
+  const size_t n = (size_t)b->n_rays * b->n_samples;
+  const int blocks = num_sms(s->device);
+  const int A = s->lay.total + (int)s->n_frames * kWidth;
+  if (n > s->tw_samples) {              // the three per-sample buffers grow together
+    size_t c0 = 0, c1 = 0, c2 = 0;
+    if (s->t_samp) cudaFree(s->t_samp);
+    if (s->t_out) cudaFree(s->t_out);
+    if (s->t_T) cudaFree(s->t_T);
+    s->t_samp = nullptr;
+    s->t_out = nullptr;
+    s->t_T = nullptr;
+    s->tw_samples = 0;
+    if ((r = grow(s->t_samp, c0, n)) != NR_OK) return r;
+    if ((r = grow(s->t_out, c1, n)) != NR_OK) return r;
+    if ((r = grow(s->t_T, c2, n)) != NR_OK) return r;
+    s->tw_samples = n;
+  }
+  if ((r = grow(s->t_raycnt, s->tw_rays, (size_t)b->n_rays)) != NR_OK) return r;
+  if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * kRows * kBwdThreads)) != NR_OK) return r;
+  const size_t n_warps = (size_t)blocks * kBwdWarps;
+  if ((r = grow(s->t_wacc, s->tw_acc, n_warps * A)) != NR_OK) return r;
+  if ((r = grow(s->t_red, s->tw_red, (size_t)A)) != NR_OK) return r;
+  if (!s->loss_acc) NR_CHECK_CUDA(cudaMalloc(&s->loss_acc, sizeof(float)));
+  if (!s->adam_m) {
+    s->n_params_total = s->n_wvol + s->n_table + s->n_mlp + s->n_res;
+    NR_CHECK_CUDA(cudaMalloc(&s->adam_m, s->n_params_total * 4));
+    NR_CHECK_CUDA(cudaMalloc(&s->adam_v, s->n_params_total * 4));
+    NR_CHECK_CUDA(cudaMemsetAsync(s->adam_m, 0, s->n_params_total * 4, st));
+    NR_CHECK_CUDA(cudaMemsetAsync(s->adam_v, 0, s->n_params_total * 4, st));
+    s->adam_t = 0;
+  }
+  NR_CHECK_CUDA(cudaMemsetAsync(s->g_wvol, 0, s->n_wvol * 4, st));
+  NR_CHECK_CUDA(cudaMemsetAsync(s->g_table, 0, s->n_table * 4, st));
+  NR_CHECK_CUDA(cudaMemsetAsync(s->t_wacc, 0, n_warps * A * 4, st));
+  NR_CHECK_CUDA(cudaMemsetAsync(s->loss_acc, 0, sizeof(float), st));
+
+  TrainDev T{};
+  T.frame_id = b->frame_id;
+  T.px = b->px;
+  T.py = b->py;
+  T.target = b->target_rgb;
+  T.n_rays = b->n_rays;
+  T.S = b->n_samples;
+  T.seed = b->step_seed;
+  for (int k = 0; k < 3; ++k) T.bg[k] = b->bg[k];
+  T.cams = s->f_cam;
+  T.fG = s->f_G;
+  T.fbias1 = s->f_bias1;
+  T.fomega = s->f_omega;
+  T.samp = s->t_samp;
+  T.out = s->t_out;
+  T.T = s->t_T;
+  T.raycnt = s->t_raycnt;
+  T.loss = s->loss_acc;
+  T.g_table = reinterpret_cast<float2 *>(s->g_table);
+  T.g_wvol = s->g_wvol;
+  T.scratch = s->t_scratch;
+  T.wacc = s->t_wacc;
+  T.acc_floats = A;
+  T.n_frames = (int)s->n_frames;
+
+  train_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
+                                                                     s->bmax[1], s->bmax[2]);
+  NR_CHECK_CUDA(cudaGetLastError());
+  const size_t smem_f = sizeof(float) * (s->lay.total + (size_t)(kWidth + kResGammaPad) * 192);
+  NR_CHECK_CUDA(cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+  train_fwd_kernel<<<blocks, 192, smem_f, st>>>(P, T);
+  NR_CHECK_CUDA(cudaGetLastError());
+  train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
+  NR_CHECK_CUDA(cudaGetLastError());
+  const size_t smem_b = sizeof(float) * s->lay.total;
+  NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);
+  NR_CHECK_CUDA(cudaGetLastError());
+  reduce_acc_kernel<<<(A + 255) / 256, 256, 0, st>>>(s->t_wacc, (int)n_warps, A, s->t_red);
+  ScatterArgs sa{};
+  sa.m = master_offsets(s);
+  sa.b = s->lay;
+  sa.g = res_gamma_dims(s);
+  sa.pose_dim = 3 * (int)s->K;
+  sa.n_frames = (int)s->n_frames;
+  sa.hidden = (int)s->hidden;
+  sa.mlp_in = (int)s->mlp_in;
+  if (s->res_enabled) {
+    scatter_res_kernel<<<(sa.m.n_res + 255) / 256, 256, 0, st>>>(s->t_red, s->f_omega, sa, s->g_res);
+  } else {
+    NR_CHECK_CUDA(cudaMemsetAsync(s->g_res, 0, s->n_res * 4, st));
+  }
+  scatter_mlp_kernel<<<(sa.m.n_mlp + 255) / 256, 256, 0, st>>>(s->t_red, sa, s->g_mlp);
+  NR_CHECK_CUDA(cudaGetLastError());
+  int launched = 7;
+  if (!(b->flags & NR_GRAD_ONLY)) {
+    const uint32_t mask = b->train_mask ? b->train_mask : NR_TRAIN_ALL;
+    s->adam_t += 1;
+    const double c1 = 1.0 / (1.0 - pow((double)b->beta1, (double)s->adam_t));
+    const double c2 = 1.0 / (1.0 - pow((double)b->beta2, (double)s->adam_t));
+    struct G_ {
+      uint32_t bit;
+      float *p, *g;
+      size_t n, off;
+    } groups[4] = {{NR_TRAIN_WVOL, s->wvol, s->g_wvol, s->n_wvol, 0},
+                   {NR_TRAIN_HASH, s->table, s->g_table, s->n_table, s->n_wvol},
+                   {NR_TRAIN_MLP, s->mlp, s->g_mlp, s->n_mlp, s->n_wvol + s->n_table},
+                   {NR_TRAIN_RES, s->res, s->g_res, s->n_res, s->n_wvol + s->n_table + s->n_mlp}};
+    for (const auto &g : groups) {
+      if (!(mask & g.bit) || (g.bit == NR_TRAIN_RES && !s->res_enabled)) continue;
+      const int nb = (int)std::min<size_t>((g.n + 255) / 256, (size_t)blocks * 8);
+      adam_kernel<<<nb, 256, 0, st>>>(g.p, g.g, s->adam_m + g.off, s->adam_v + g.off, g.n, b->lr, b->beta1, b->beta2,
+                                      b->eps, (float)c1, (float)c2);
+      ++launched;
+    }
+    NR_CHECK_CUDA(cudaGetLastError());
+    s->params_dirty = true;
+    s->bias_dirty = true;
+  }
+  count_launches(launched);
+  if (loss_out) {
+    NR_CHECK_CUDA(cudaMemcpyAsync(loss_out, s->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st));
+    NR_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  return NR_OK;
 }
