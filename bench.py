@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-pixels", type=int, default=4096)
+    p.add_argument("--train-steps", type=int, default=5)
+    p.add_argument("--train-only", action="store_true", help="time only the training step")
+    p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
     return p.parse_args()
 
 
@@ -139,6 +142,55 @@ def cpu_baseline(cfg, poses, n_pixels, seed=0):
                        f"FP64 torch CPU, no early termination), {dt:.1f} s")
 
 
+def train_bench(nr, device, steps, warmup=2, n=1 << 18):
+    """Training-step time on the training workload: 16 frames of 512x512 with seeded
+    poses, targets rendered from a seeded ground-truth field of the tiny workload's
+    shape, 2^18 random pixel rays x 128 stratified samples, forward + backward +
+    Adam (lr 1e-2, beta (0.9, 0.99)).  CUDA events on the training stream."""
+    import torch
+    from paper_2306_16541_gb300 import synth
+    gt = synth.subject(700, hash_scale=0.5, res_last_std=0.02)
+    gt["mlp_layers"][-1][1][3] = 3.0
+    gt["mlp_params"] = synth.pack_layers(gt["mlp_layers"])
+    trainee = synth.subject(700)
+    frames = synth.training_frames(701, 16, res=512)
+    G = nr.Subject(gt, device=device)
+    targets = []
+    for i, cam in enumerate(frames["cameras"]):
+        G.set_pose(frames["axis_angle"][i], frames["root_t"][i])
+        targets.append(G.render(cam, nr.make_opts("f32"))[..., :3].clone())
+    G.close()
+    targets = torch.stack(targets)
+    Sub = nr.Subject(trainee, device=device)
+    Sub.set_frames(frames["axis_angle"], frames["root_t"], frames["cameras"])
+    gen = torch.Generator(device="cuda").manual_seed(702)
+    batches = []
+    for _ in range(steps + warmup):
+        f = torch.randint(0, 16, (n,), device="cuda", generator=gen, dtype=torch.int32)
+        px = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
+        py = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
+        batches.append((f, px, py, targets[f.long(), py.long(), px.long()].contiguous()))
+    losses = []
+    for k in range(warmup):
+        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE))
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(warmup, warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE))
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    Sub.close()
+    return {"workload": f"16 frames 512x512, {n} rays x 128 samples, fp32 forward+backward+Adam",
+            "lr": "1e-2 (hash, canonical MLP), 1e-3 (weight volume, residual MLP)",
+            "ms": statistics.mean(ms), "ms_min": min(ms), "steps": steps, "warmup": warmup,
+            "rays_per_s": n / (statistics.mean(ms) / 1000.0),
+            "samples_per_s": n * 128 / (statistics.mean(ms) / 1000.0),
+            "loss_first": losses[0], "loss_last": losses[-1]}
+
+
 def run_reference(a):
     rank, world, local = dist_setup(a.gpus)
     if rank != 0:
@@ -171,6 +223,9 @@ def run_ours(a):
         build.build()
     barrier(world)
     from paper_2306_16541_gb300 import nr
+    if a.train_only:
+        print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays)}))
+        return
 
     cfg, poses = workload()
     cam = nr.make_camera(cfg["camera"])
@@ -225,6 +280,8 @@ def run_ours(a):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = world * n_rays * a.steps / e2e_s
 
+    train = train_bench(nr, local, a.train_steps, n=a.train_rays) if a.train_steps > 0 else None
+
     field_ms = statistics.mean(s["field_ms"] for s in stages)
     live = statistics.mean(s["live_samples"] for s in stages)
     s = cfg["subject"]
@@ -258,6 +315,7 @@ def run_ours(a):
                      "traffic": float(traffic) if traffic else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},
+        "train_step": train,
         "gpu_launches": launches,
         "clocks": clk,
     }

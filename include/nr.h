@@ -221,6 +221,9 @@ typedef struct {
   float hann_alpha;              /* residual PE window; < 0 = all bands */
   uint32_t flags;                /* NR_GRAD_ONLY */
   uint32_t train_mask;           /* NR_TRAIN_* groups that are updated; 0 = all */
+  float lr_scale[4];             /* per-group multiplier of lr: weight volume, hash table,
+                                    canonical MLP, residual MLP; 0 means 1.  Sec. 5.2 trains
+                                    the NeRF network with a 10x larger rate than the others. */
 } nr_train_batch;
 
 /* Forward, loss L = mean over rays and channels of (C^ - C_gt)^2, the

@@ -10,8 +10,8 @@
 //   * MLP weight gradients dW = sum_s delta_s (x) h_s are reduced per warp:
 //     after a tile of 32 samples, every lane owns two output rows of a layer
 //     and sums the 32 samples' products for them, then adds the result into
-//     that warp's private accumulator (plain read-modify-write, no atomics);
-//     one reduction kernel sums the private accumulators at the end.
+//     its block's private accumulator (fire-and-forget atomics shared by the
+//     block's 4 warps only); one kernel sums the block accumulators at the end.
 //   * each thread keeps its forward activations and backward deltas in its
 //     own column of an L2-resident scratch buffer, which the warp reads back
 //     in the reduction.
@@ -26,18 +26,35 @@ namespace nr {
 constexpr int kBwdThreads = 128;
 constexpr int kBwdWarps = kBwdThreads / 32;
 
-// Rows of a thread's scratch column.
-constexpr int R_GAM = 0;                        // gamma(x_skel)            48
-constexpr int R_RH = R_GAM + kResGammaPad;      // residual h1..h4          4 x 64
-constexpr int R_ENC = R_RH + 4 * kWidth;        // hash encoding            32
-constexpr int R_CH = R_ENC + kMlpIn;            // canonical h1..hH         4 x 64
-constexpr int D_C = R_CH + kMaxHidden * kWidth; // canonical deltas h1..hH  4 x 64, then output 4
-constexpr int D_CL_MAX = D_C + kMaxHidden * kWidth;
-constexpr int D_R = D_CL_MAX + 4;               // residual deltas h1..h4   4 x 64, then output 4
-constexpr int D_R5 = D_R + 4 * kWidth;
-constexpr int R_DENC = D_R5 + 4;                // dL/d encoding            32
-constexpr int R_DGAM = R_DENC + kMlpIn;         // dL/d gamma               48
-constexpr int kRows = R_DGAM + kResGammaPad;
+// Rows of a thread's scratch column (sized for the subject's hidden depth H).
+struct Rows {
+  int gam;     // gamma(x_skel)            48
+  int rh;      // residual h1..h4          4 x 64
+  int enc;     // hash encoding            32
+  int ch;      // canonical h1..hH         H x 64
+  int dc;      // canonical deltas h1..hH  H x 64, then the output's 4
+  int dr;      // residual deltas h1..h4   4 x 64
+  int dr5;     // residual output delta    4
+  int denc;    // dL/d encoding            32
+  int dgam;    // dL/d gamma               48
+  int total;
+};
+
+static Rows make_rows(int H) {
+  Rows r{};
+  int o = 0;
+  r.gam = o; o += kResGammaPad;
+  r.rh = o; o += 4 * kWidth;
+  r.enc = o; o += kMlpIn;
+  r.ch = o; o += H * kWidth;
+  r.dc = o; o += H * kWidth + 4;
+  r.dr = o; o += 4 * kWidth;
+  r.dr5 = o; o += 4;
+  r.denc = o; o += kMlpIn;
+  r.dgam = o; o += kResGammaPad;
+  r.total = o;
+  return r;
+}
 
 struct TrainDev {
   const uint32_t *frame_id, *px, *py;
@@ -54,8 +71,9 @@ struct TrainDev {
   float2 *g_table;
   float *g_wvol;
   float *scratch, *wacc;
-  int acc_floats;         // floats per warp accumulator
+  int acc_floats;         // floats per block accumulator
   int n_frames;
+  Rows rw;
 };
 
 // ----------------------------------------------------------------- rays
@@ -205,6 +223,7 @@ __device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const f
 }
 
 // Warp-level weight gradient of one layer with 64 outputs: acc[wt + k*64 + j] += sum_s h[s][k] d[s][j],
+// added with fire-and-forget atomics into the block's accumulator (shared by its warps),
 // acc[b + j] += sum_s d[s][j]; lane owns j = lane and lane + 32.  `wcol` points at the warp's
 // column 0 (so row r of sample s is wcol[r * stride + s]).
 __device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in, int n_in, int r_d, float *acc,
@@ -226,8 +245,8 @@ __device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in,
       s0 += d0[s];
       s1 += d1[s];
     }
-    acc[b + lane] += s0;
-    acc[b + lane + 32] += s1;
+    atomicAdd(acc + b + lane, s0);
+    atomicAdd(acc + b + lane + 32, s1);
   }
   for (int k = 0; k < n_in; ++k) {
     const float4 *ph = reinterpret_cast<const float4 *>(wcol + (r_in + k) * stride);
@@ -238,8 +257,8 @@ __device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in,
       a0 = fmaf(h.x, d0[4 * q], fmaf(h.y, d0[4 * q + 1], fmaf(h.z, d0[4 * q + 2], fmaf(h.w, d0[4 * q + 3], a0))));
       a1 = fmaf(h.x, d1[4 * q], fmaf(h.y, d1[4 * q + 1], fmaf(h.z, d1[4 * q + 2], fmaf(h.w, d1[4 * q + 3], a1))));
     }
-    acc[wt + k * kWidth + lane] += a0;
-    acc[wt + k * kWidth + lane + 32] += a1;
+    atomicAdd(acc + wt + k * kWidth + lane, a0);
+    atomicAdd(acc + wt + k * kWidth + lane + 32, a1);
   }
 }
 
@@ -266,9 +285,9 @@ __device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, 
       a1 = fmaf(h1[4 * q], d.x, fmaf(h1[4 * q + 1], d.y, fmaf(h1[4 * q + 2], d.z, fmaf(h1[4 * q + 3], d.w, a1))));
       sb += d.x + d.y + d.z + d.w;
     }
-    acc[wt + lane * 4 + j] += a0;
-    acc[wt + (lane + 32) * 4 + j] += a1;
-    if (lane == 0) acc[b + j] += sb;
+    atomicAdd(acc + wt + lane * 4 + j, a0);
+    atomicAdd(acc + wt + (lane + 32) * 4 + j, a1);
+    if (lane == 0) atomicAdd(acc + b + j, sb);
   }
 }
 
@@ -283,10 +302,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
   const BlobLayout &Ly = P.lay;
   const int stride = blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Rows &RW = T.rw;
+  const int R_GAM = RW.gam, R_RH = RW.rh, R_ENC = RW.enc, R_CH = RW.ch, D_C = RW.dc, D_R = RW.dr, D_R5 = RW.dr5,
+            R_DENC = RW.denc, R_DGAM = RW.dgam, kRows = RW.total;
   float *colbase = T.scratch + (size_t)blockIdx.x * kRows * stride;
   float *col = colbase + threadIdx.x;                  // this thread's column
   const float *wcol = colbase + warp * 32;             // the warp's column 0
-  float *acc = T.wacc + ((size_t)blockIdx.x * kBwdWarps + warp) * T.acc_floats;
+  float *acc = T.wacc + (size_t)blockIdx.x * T.acc_floats;
   float *accF = acc + Ly.total;                        // per-frame first-layer bias gradients [F][64]
   const int H = P.hidden;
   const uint32_t n = T.n_rays * T.S;
@@ -511,8 +533,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         const int fr = (int)T.frame_id[jj / T.S];
         if (fr != cur) {
           if (cur >= 0) {
-            accF[cur * kWidth + lane] += s0;
-            accF[cur * kWidth + lane + 32] += s1;
+            atomicAdd(accF + cur * kWidth + lane, s0);
+            atomicAdd(accF + cur * kWidth + lane + 32, s1);
           }
           cur = fr;
           s0 = s1 = 0.f;
@@ -521,15 +543,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         s1 += d1[sI];
       }
       if (cur >= 0) {
-        accF[cur * kWidth + lane] += s0;
-        accF[cur * kWidth + lane + 32] += s1;
+        atomicAdd(accF + cur * kWidth + lane, s0);
+        atomicAdd(accF + cur * kWidth + lane + 32, s1);
       }
     }
     __syncwarp();
   }
 }
 
-// Sum of the per-warp accumulators: red[e] = sum_w wacc[w][e].
+// Sum of the per-block accumulators: red[e] = sum_w wacc[w][e].
 __global__ void reduce_acc_kernel(const float *__restrict__ wacc, int n_warps, int A, float *__restrict__ red) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A) return;
@@ -642,6 +664,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_REQUIRE((uint64_t)b->n_rays * b->n_samples <= (1ull << 31), "nr_train_step: batch too large");
   NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
              "nr_train_step: bad Adam hyper-parameters");
+  for (int k = 0; k < 4; ++k) NR_REQUIRE(b->lr_scale[k] >= 0.f, "nr_train_step: negative lr_scale");
   if (s->n_frames == 0) {
     set_error("nr_train_step: call nr_set_frames first");
     return NR_ESTATE;
@@ -674,9 +697,10 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
     s->tw_samples = n;
   }
   if ((r = grow(s->t_raycnt, s->tw_rays, (size_t)b->n_rays)) != NR_OK) return r;
-  if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * kRows * kBwdThreads)) != NR_OK) return r;
-  const size_t n_warps = (size_t)blocks * kBwdWarps;
-  if ((r = grow(s->t_wacc, s->tw_acc, n_warps * A)) != NR_OK) return r;
+  const Rows rows = make_rows((int)s->hidden);
+  if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * rows.total * kBwdThreads)) != NR_OK) return r;
+  const size_t n_acc = (size_t)blocks;                 // one accumulator per block
+  if ((r = grow(s->t_wacc, s->tw_acc, n_acc * A)) != NR_OK) return r;
   if ((r = grow(s->t_red, s->tw_red, (size_t)A)) != NR_OK) return r;
   if (!s->loss_acc) NR_CHECK_CUDA(cudaMalloc(&s->loss_acc, sizeof(float)));
   if (!s->adam_m) {
@@ -689,7 +713,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   }
   NR_CHECK_CUDA(cudaMemsetAsync(s->g_wvol, 0, s->n_wvol * 4, st));
   NR_CHECK_CUDA(cudaMemsetAsync(s->g_table, 0, s->n_table * 4, st));
-  NR_CHECK_CUDA(cudaMemsetAsync(s->t_wacc, 0, n_warps * A * 4, st));
+  NR_CHECK_CUDA(cudaMemsetAsync(s->t_wacc, 0, n_acc * A * 4, st));
   NR_CHECK_CUDA(cudaMemsetAsync(s->loss_acc, 0, sizeof(float), st));
 
   TrainDev T{};
@@ -716,6 +740,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.wacc = s->t_wacc;
   T.acc_floats = A;
   T.n_frames = (int)s->n_frames;
+  T.rw = rows;
 
   train_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
                                                                      s->bmax[1], s->bmax[2]);
@@ -730,7 +755,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);
   NR_CHECK_CUDA(cudaGetLastError());
-  reduce_acc_kernel<<<(A + 255) / 256, 256, 0, st>>>(s->t_wacc, (int)n_warps, A, s->t_red);
+  reduce_acc_kernel<<<(A + 255) / 256, 256, 0, st>>>(s->t_wacc, (int)n_acc, A, s->t_red);
   ScatterArgs sa{};
   sa.m = master_offsets(s);
   sa.b = s->lay;
@@ -756,14 +781,16 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
       uint32_t bit;
       float *p, *g;
       size_t n, off;
-    } groups[4] = {{NR_TRAIN_WVOL, s->wvol, s->g_wvol, s->n_wvol, 0},
-                   {NR_TRAIN_HASH, s->table, s->g_table, s->n_table, s->n_wvol},
-                   {NR_TRAIN_MLP, s->mlp, s->g_mlp, s->n_mlp, s->n_wvol + s->n_table},
-                   {NR_TRAIN_RES, s->res, s->g_res, s->n_res, s->n_wvol + s->n_table + s->n_mlp}};
+      float scale;
+    } groups[4] = {{NR_TRAIN_WVOL, s->wvol, s->g_wvol, s->n_wvol, 0, b->lr_scale[0]},
+                   {NR_TRAIN_HASH, s->table, s->g_table, s->n_table, s->n_wvol, b->lr_scale[1]},
+                   {NR_TRAIN_MLP, s->mlp, s->g_mlp, s->n_mlp, s->n_wvol + s->n_table, b->lr_scale[2]},
+                   {NR_TRAIN_RES, s->res, s->g_res, s->n_res, s->n_wvol + s->n_table + s->n_mlp, b->lr_scale[3]}};
     for (const auto &g : groups) {
       if (!(mask & g.bit) || (g.bit == NR_TRAIN_RES && !s->res_enabled)) continue;
+      const float lr = b->lr * (g.scale > 0.f ? g.scale : 1.f);
       const int nb = (int)std::min<size_t>((g.n + 255) / 256, (size_t)blocks * 8);
-      adam_kernel<<<nb, 256, 0, st>>>(g.p, g.g, s->adam_m + g.off, s->adam_v + g.off, g.n, b->lr, b->beta1, b->beta2,
+      adam_kernel<<<nb, 256, 0, st>>>(g.p, g.g, s->adam_m + g.off, s->adam_v + g.off, g.n, lr, b->beta1, b->beta2,
                                       b->eps, (float)c1, (float)c2);
       ++launched;
     }

@@ -24,6 +24,9 @@ NR_POSE_MATRICES = 1
 NR_GRAD_ONLY = 1
 NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_ALL = 1, 2, 4, 8, 15
 NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES = range(4)
+# Per-group learning-rate multipliers (weight volume, hash, canonical MLP, residual MLP):
+# Sec. 5.2 uses a 10x smaller rate for the networks other than the NeRF network.
+PAPER_LR_SCALE = (0.1, 1.0, 1.0, 0.1)
 NR_QUERY_STRIDE = 12
 NR_RENDER_PROFILE = 1
 NR_ABI_VERSION = 1
@@ -63,7 +66,7 @@ class nr_train_batch(C.Structure):
                 ("target_rgb", _fp), ("n_samples", C.c_uint32), ("bg", C.c_float * 3),
                 ("step_seed", C.c_uint64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("hann_alpha", C.c_float), ("flags", C.c_uint32),
-                ("train_mask", C.c_uint32)]
+                ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4)]
 
 
 def _load() -> C.CDLL:
@@ -291,7 +294,8 @@ class Subject:
 
     def train_step(self, frame_id, px, py, target_rgb, n_samples: int, step_seed: int, lr: float = 1e-2,
                    betas=(0.9, 0.99), eps: float = 1e-8, bg=(0.0, 0.0, 0.0), hann_alpha: float = -1.0,
-                   grad_only: bool = False, train_mask: int = 0, stream=None) -> float:
+                   grad_only: bool = False, train_mask: int = 0, lr_scale=(0.0, 0.0, 0.0, 0.0),
+                   stream=None) -> float:
         b = nr_train_batch()
         b.n_rays = int(frame_id.shape[0])
         b.frame_id = C.cast(C.c_void_p(frame_id.data_ptr()), _up)
@@ -302,6 +306,7 @@ class Subject:
         b.bg[:] = [float(v) for v in bg]
         b.lr, b.beta1, b.beta2, b.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
         b.hann_alpha, b.flags, b.train_mask = float(hann_alpha), NR_GRAD_ONLY if grad_only else 0, int(train_mask)
+        b.lr_scale[:] = [float(v) for v in lr_scale]
         return nr_train_step(self.h, b, stream)
 
     def param(self, which: int):
