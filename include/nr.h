@@ -243,6 +243,66 @@ nr_status nr_train_step(nr_subject *s, const nr_train_batch *batch, float *loss_
 nr_status nr_param(nr_subject *s, uint32_t which, float **dev_ptr, float **grad_ptr, size_t *count);
 nr_status nr_params_changed(nr_subject *s);
 
+/* ---------------------------------------------------------------- serving
+ * A persistent render server for the multi-user conferencing scenario the
+ * paper envisions (Sec. 3, Sec. 6: many people rendered for many viewers).
+ * Registered subjects stay resident on the device.  Requests (subject,
+ * camera, pose, options, output) are admitted in arrival order into slots,
+ * each with its own stream, pose buffers, posed occupancy bitfield and work
+ * queues; a slot is created only while the device-memory budget (max_bytes)
+ * and the slot limit allow, and is reused afterwards.  A request is enqueued
+ * on its slot's stream as soon as it is admitted, so requests arriving while
+ * others are on the GPU start at once and their kernels overlap (continuous
+ * batching).  Each result is the same as rendering the request alone with
+ * nr_set_pose + nr_render.  Latency is measured from nr_server_submit to the
+ * completion of the request's last GPU operation.  Every wait is bounded. */
+typedef struct nr_server nr_server;   /* opaque */
+
+typedef struct {
+  uint32_t subject;          /* index from nr_server_add_subject */
+  nr_camera cam;
+  float axis_angle[72];      /* pose: [24][3] joint rotations (axis * angle) */
+  float root_t[3];
+  nr_render_opts opts;       /* NR_RENDER_PROFILE is ignored */
+  float *out_rgba;           /* caller-owned [H][W][4]: device memory or pinned host memory,
+                                valid until the request completes */
+} nr_request;
+
+typedef struct {
+  uint64_t submitted, completed, failed, rejected;
+  uint32_t active;           /* requests on the GPU now */
+  uint32_t queued;           /* requests waiting for a slot */
+  uint32_t slots, peak_active;
+  uint64_t bytes_in_use;     /* device memory held by slots */
+  double rays_done;
+} nr_server_stats;
+
+/* Creates a server on `device` with a device-memory budget for its slots
+ * (each slot needs about 136 MiB) and a slot limit (1..256); starts its
+ * worker thread.  NR_EINVAL if max_bytes cannot hold one slot. */
+nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t max_slots, nr_server **out);
+/* Registers a subject (not owned; it must outlive the server and must not be
+ * trained or given new parameters while the server runs).  All subjects must
+ * share one occupancy grid size. */
+nr_status nr_server_add_subject(nr_server *srv, nr_subject *s, uint32_t *index);
+/* Queues a request (copied); *id identifies it.  NR_EINVAL for bad fields or a
+ * pageable host output; NR_ESTATE once the server is stopping. */
+nr_status nr_server_submit(nr_server *srv, const nr_request *req, uint64_t *id);
+/* state: 0 queued, 1 running, 2 done, -1 failed; a finished request is
+ * forgotten after it has been reported once. */
+nr_status nr_server_poll(nr_server *srv, uint64_t id, int32_t *state, double *latency_ms);
+/* Waits at most timeout_ms for request `id`: NR_OK when done (latency in
+ * *latency_ms, may be NULL), NR_ETIMEOUT if still pending, NR_ECUDA if the
+ * request failed. */
+nr_status nr_server_wait(nr_server *srv, uint64_t id, uint32_t timeout_ms, double *latency_ms);
+nr_status nr_server_get_stats(nr_server *srv, nr_server_stats *out);
+/* Refuses new requests and waits at most timeout_ms for the queued and running
+ * ones to finish: NR_OK when drained (the worker has exited), NR_ETIMEOUT
+ * otherwise (call again to keep waiting). */
+nr_status nr_server_stop(nr_server *srv, uint32_t timeout_ms);
+/* Stops (draining, waiting up to 10 minutes), then frees every slot.  NULL is a no-op. */
+nr_status nr_server_destroy(nr_server *srv);
+
 /* Copies the current pose's float32 transforms G[n_bones][12] (host). */
 nr_status nr_pose_transforms(nr_subject *s, float *G_out);
 /* Copies the current posed occupancy bitfield (occ_grid^3 / 32 uint32, host);

@@ -186,6 +186,9 @@ struct MasterOffsets {
 MasterOffsets master_offsets(const nr_subject *s);
 int res_gamma_dims(const nr_subject *s);
 void count_launches(uint64_t n);                              // kernels launched by the library
+void forward_kinematics(const nr_subject *s, const float *aa, const float *root_t, float *G);   // host, fp64 -> fp32
+nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, uint32_t *bits, cudaStream_t st);
+nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *bias_dev, int n_poses, cudaStream_t st);
 bool subject_ok(const nr_subject *s);
 nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs
 nr_status ensure_bias(nr_subject *s, cudaStream_t st);         // pose-folded bias

@@ -253,6 +253,42 @@ nr_status grow_workspace(nr_subject *s, size_t rays, size_t samples) {
   return NR_OK;
 }
 
+nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
+                       const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st) {
+  const CamParams C = cam_params(cam);
+  const uint32_t n_rays = cam->width * cam->height;
+  const uint32_t chunk = (uint32_t)std::min<uint64_t>(
+      std::min<uint64_t>(n_rays, w.cap_rays), std::max<uint64_t>(1, w.cap_samples / cam->n_samples));
+  if (chunk == 0) {
+    set_error("render_frame: workspace too small for one ray");
+    return NR_EINVAL;
+  }
+  MarchParams mp{};
+  for (int k = 0; k < 3; ++k) {
+    mp.bmin[k] = s->bmin[k];
+    mp.bmax[k] = s->bmax[k];
+  }
+  mp.grid = (int)s->occ_grid;
+  mp.bits = opts->use_occupancy ? bits : nullptr;
+  nr_status r;
+  for (uint32_t r0 = 0; r0 < n_rays; r0 += chunk) {
+    const uint32_t nr_ = std::min(chunk, n_rays - r0);
+    mp.ray0 = r0;
+    mp.ray_end = r0 + nr_;
+    NR_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(uint32_t), st));
+    march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, w.samp, w.ray_range, w.counter);
+    NR_CHECK_CUDA(cudaGetLastError());
+    if ((r = launch_field(P, opts->mlp_dtype, kModeRender, w.samp, 0, w.counter, (float *)w.samp_out, s->device,
+                          st)) != NR_OK)
+      return r;
+    composite_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, cam->bg[0],
+                                                        cam->bg[1], cam->bg[2], dst + r0);
+    NR_CHECK_CUDA(cudaGetLastError());
+    count_launches(3);
+  }
+  return NR_OK;
+}
+
 }  // namespace nr
 
 using namespace nr;

@@ -82,6 +82,18 @@ __global__ void march_kernel(CamParams cam, MarchParams mp, float4 *__restrict__
 __global__ void composite_kernel(const uint2 *__restrict__ ray_range, const float4 *__restrict__ so, uint32_t n_rays,
                                  float t_min, float bg0, float bg1, float bg2, float4 *__restrict__ out);
 
+// Explicit work buffers of one frame render (the serving loop gives each request its own).
+struct FrameWork {
+  float4 *samp, *samp_out;        // [cap_samples]
+  uint2 *ray_range;               // [cap_rays]
+  uint32_t *counter;              // [1]
+  size_t cap_samples, cap_rays;
+};
+// Renders `cam` for the pose whose transforms / folded bias are in P (P.G, P.bias1) and whose posed
+// occupancy bitfield is `bits` into the device buffer dst[height * width], in ray chunks that fit w.
+nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
+                       const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st);
+
 CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,

@@ -60,7 +60,7 @@ static void rodrigues(const double a[3], double R[9]) {
   for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + s * K[i] + c1 * KK[i];
 }
 
-static void forward_kinematics(const nr_subject *s, const float *aa, const float *root_t, float *G) {
+void forward_kinematics(const nr_subject *s, const float *aa, const float *root_t, float *G) {
   const int K = (int)s->K;
   std::vector<double> AR(K * 9), At(K * 3);
   for (int i = 0; i < K; ++i) {
@@ -370,6 +370,23 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   s->params_dirty = false;
   s->bias_dirty = true;
   (void)P;
+  return NR_OK;
+}
+
+nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, uint32_t *bits, cudaStream_t st) {
+  const int g = (int)s->occ_grid;
+  const long n = (long)g * g * g;
+  posed_bitfield_kernel<<<nblk(n, 256), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
+                                                      s->bmax[1], s->bmax[2], g, bits);
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(1);
+  return NR_OK;
+}
+
+nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *bias_dev, int n_poses, cudaStream_t st) {
+  fold_pose_bias_kernel<<<n_poses, kWidth, 0, st>>>(s->res, res_gamma_dims(s), 3 * (int)s->K, omega_dev, bias_dev);
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(1);
   return NR_OK;
 }
 

@@ -69,6 +69,18 @@ class nr_train_batch(C.Structure):
                 ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4)]
 
 
+class nr_request(C.Structure):
+    _fields_ = [("subject", C.c_uint32), ("cam", nr_camera), ("axis_angle", C.c_float * 72),
+                ("root_t", C.c_float * 3), ("opts", nr_render_opts), ("out_rgba", C.c_void_p)]
+
+
+class nr_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("rejected", C.c_uint64), ("active", C.c_uint32), ("queued", C.c_uint32),
+                ("slots", C.c_uint32), ("peak_active", C.c_uint32), ("bytes_in_use", C.c_uint64),
+                ("rays_done", C.c_double)]
+
+
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2306_16541_gb300.build.build()")
@@ -89,6 +101,14 @@ def _load() -> C.CDLL:
         "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
+        "nr_server_create": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(vp)], C.c_int),
+        "nr_server_add_subject": ([vp, vp, C.POINTER(C.c_uint32)], C.c_int),
+        "nr_server_submit": ([vp, C.POINTER(nr_request), C.POINTER(C.c_uint64)], C.c_int),
+        "nr_server_poll": ([vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
+        "nr_server_wait": ([vp, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)], C.c_int),
+        "nr_server_get_stats": ([vp, C.POINTER(nr_server_stats)], C.c_int),
+        "nr_server_stop": ([vp, C.c_uint32], C.c_int),
+        "nr_server_destroy": ([vp], C.c_int),
         "nr_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -328,6 +348,66 @@ class Subject:
         if getattr(self, "h", None) is not None:
             nr_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The continuous-batching render server (nr_server_*)."""
+
+    def __init__(self, max_bytes: int, max_slots: int, device: int = 0):
+        self.h = C.c_void_p()
+        check(lib.nr_server_create(device, int(max_bytes), int(max_slots), C.byref(self.h)), "nr_server_create")
+        self.subjects = []
+
+    def add_subject(self, subject: Subject) -> int:
+        idx = C.c_uint32()
+        check(lib.nr_server_add_subject(self.h, subject.h, C.byref(idx)), "nr_server_add_subject")
+        self.subjects.append(subject)
+        return int(idx.value)
+
+    @staticmethod
+    def request(subject: int, cam, axis_angle, root_t, opts, out) -> nr_request:
+        r = nr_request()
+        r.subject = int(subject)
+        r.cam = cam if isinstance(cam, nr_camera) else make_camera(cam)
+        r.axis_angle[:] = [float(v) for v in np.asarray(axis_angle, np.float32).ravel()]
+        r.root_t[:] = [float(v) for v in np.asarray(root_t if root_t is not None else np.zeros(3), np.float32)]
+        r.opts = opts
+        r.out_rgba = out.data_ptr() if hasattr(out, "data_ptr") else int(out)
+        return r
+
+    def submit(self, req: nr_request) -> int:
+        rid = C.c_uint64()
+        check(lib.nr_server_submit(self.h, C.byref(req), C.byref(rid)), "nr_server_submit")
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> float:
+        lat = C.c_double()
+        check(lib.nr_server_wait(self.h, rid, int(timeout_ms), C.byref(lat)), "nr_server_wait")
+        return float(lat.value)
+
+    def poll(self, rid: int):
+        state, lat = C.c_int32(), C.c_double()
+        check(lib.nr_server_poll(self.h, rid, C.byref(state), C.byref(lat)), "nr_server_poll")
+        return int(state.value), float(lat.value)
+
+    def stats(self) -> dict:
+        st = nr_server_stats()
+        check(lib.nr_server_get_stats(self.h, C.byref(st)), "nr_server_get_stats")
+        return {k: getattr(st, k) for k, _ in nr_server_stats._fields_}
+
+    def stop(self, timeout_ms: int = 60000) -> None:
+        check(lib.nr_server_stop(self.h, int(timeout_ms)), "nr_server_stop")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            check(lib.nr_server_destroy(self.h), "nr_server_destroy")
+            self.h = C.c_void_p()
 
     def __del__(self):
         try:

@@ -161,7 +161,7 @@ ELLIPSOID_FLOATS = 15   # centre[3], rotation rows[9] (canonical -> local), radi
 
 
 def ellipsoids(rng: np.random.Generator, joints: np.ndarray,
-               target_frac: float = 0.15, grid: int = 64) -> np.ndarray:
+               target_frac: float = 0.15, grid: int = 40) -> np.ndarray:
     """One canonical ellipsoid per bone segment, inflated until ~target_frac of
     the box is covered at the rest pose (measured on a coarse grid).
 
@@ -198,7 +198,7 @@ def ellipsoids(rng: np.random.Generator, joints: np.ndarray,
         return inside.mean()
 
     lo, hi = 0.01, 0.6
-    for _ in range(30):                 # bisection on the tube radius
+    for _ in range(16):                 # bisection on the tube radius
         mid = 0.5 * (lo + hi)
         lo, hi = (mid, hi) if frac(mid) < target_frac else (lo, mid)
     r = radii(0.5 * (lo + hi))
