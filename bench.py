@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
     p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
+    p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
+    p.add_argument("--serve-only", action="store_true", help="run only the serving scenario")
     return p.parse_args()
 
 
@@ -191,6 +193,76 @@ def train_bench(nr, device, steps, warmup=2, n=1 << 18):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
+def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slots=16):
+    """Multi-user serving: n_subjects frame-workload subjects resident on the device, Poisson
+    arrivals at `rate` req/s for `duration` s, each request a random subject, a camera on the
+    2.5 m sphere, a fresh pose (<= 30 deg per bone) and 256^2 / 512^2 / 1024^2 with probabilities
+    0.3 / 0.5 / 0.2, 128 samples, occupancy, ERT.  Latency = submit to completion.  The same
+    requests are then rendered one at a time through nr_set_pose + nr_render (a plain queue)."""
+    import torch
+    from paper_2306_16541_gb300 import synth
+    subs = [nr.Subject(synth.config_frame512(seed=3000 + i)["subject"], device=device) for i in range(n_subjects)]
+    reqs = synth.request_stream(3100, n_subjects, rate, duration)
+    opts = nr.make_opts(mlp, "f16", True, 1e-4)
+    sizes = [q["camera"].width * q["camera"].height for q in reqs]
+    arena = torch.empty(sum(sizes) * 4, device="cuda")
+    outs, off = [], 0
+    for n in sizes:
+        outs.append(arena[off:off + 4 * n])
+        off += 4 * n
+    srv = nr.Server(max_bytes=max_slots * (137 << 20), max_slots=max_slots, device=device)
+    for S in subs:
+        srv.add_subject(S)
+    # warm-up: one request per resolution
+    warm = [srv.submit(srv.request(0, q["camera"], q["axis_angle"], q["root_t"], opts, outs[i]))
+            for i, q in enumerate(reqs[:6])]
+    for w in warm:
+        srv.wait(w, 120000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids = []
+    for i, q in enumerate(reqs):
+        dt = t0 + q["t_arrive"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(srv.request(q["subject"], q["camera"], q["axis_angle"], q["root_t"], opts, outs[i])))
+    lat = [srv.wait(i, 600000) for i in ids]
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    by_res = {}
+    for q, l in zip(reqs, lat):
+        by_res.setdefault(q["camera"].width, []).append(l)
+    # one at a time through the plain path (service times), then a FIFO queue over the same arrivals
+    service = []
+    for i, q in enumerate(reqs):
+        S = subs[q["subject"]]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        S.set_pose(q["axis_angle"], q["root_t"])
+        nr.nr_render(S.h, nr.make_camera(q["camera"]), opts, outs[i])
+        e1.record()
+        torch.cuda.synchronize()
+        service.append(e0.elapsed_time(e1))
+    for S in subs:
+        S.close()
+    fifo, t_free = [], 0.0
+    for q, sv in zip(reqs, service):
+        start = max(q["t_arrive"] * 1000.0, t_free)
+        t_free = start + sv
+        fifo.append(t_free - q["t_arrive"] * 1000.0)
+    pct = lambda v, p: float(np.percentile(np.asarray(v), p))
+    return {"workload": f"{n_subjects} subjects (512^2-workload fields, bf16 MLP), Poisson {rate:g} req/s for "
+                        f"{duration:g} s, 256/512/1024 px at 0.3/0.5/0.2, 128 samples, occupancy + ERT",
+            "requests": len(reqs), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": max(lat),
+            "p50_ms_by_res": {str(k): pct(v, 50) for k, v in sorted(by_res.items())},
+            "p99_ms_by_res": {str(k): pct(v, 99) for k, v in sorted(by_res.items())},
+            "rays_per_s": sum(sizes) / (t_end - t0), "peak_active": st["peak_active"], "slots": st["slots"],
+            "one_at_a_time": {"rays_per_s": sum(sizes) / (sum(service) / 1000.0),
+                              "p50_ms": pct(fifo, 50), "p99_ms": pct(fifo, 99),
+                              "mean_service_ms": float(np.mean(service))}}
+
+
 def run_reference(a):
     rank, world, local = dist_setup(a.gpus)
     if rank != 0:
@@ -225,6 +297,9 @@ def run_ours(a):
     from paper_2306_16541_gb300 import nr
     if a.train_only:
         print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays)}))
+        return
+    if a.serve_only:
+        print(json.dumps({"serving": serve_bench(nr, local, a.mlp, duration=a.serve_seconds)}))
         return
 
     cfg, poses = workload()
@@ -281,6 +356,7 @@ def run_ours(a):
     e2e_value = world * n_rays * a.steps / e2e_s
 
     train = train_bench(nr, local, a.train_steps, n=a.train_rays) if a.train_steps > 0 else None
+    serving = serve_bench(nr, local, a.mlp, duration=a.serve_seconds) if a.serve_seconds > 0 else None
 
     field_ms = statistics.mean(s["field_ms"] for s in stages)
     live = statistics.mean(s["live_samples"] for s in stages)
@@ -316,6 +392,7 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},
         "train_step": train,
+        "serving": serving,
         "gpu_launches": launches,
         "clocks": clk,
     }

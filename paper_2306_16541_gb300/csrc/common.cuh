@@ -71,6 +71,7 @@ struct FieldParams {
   float box_c[3], box_ih[3];         // box centre and 2 / (bmax - bmin)
   int wres;
   const float *wvol;                 // [25][R^3]
+  const float4 *wquad;               // [24][(R+2)(R+1)(R+1)] corner blocks (see build_quad_kernel)
   int L;
   uint32_t T_mask;
   uint32_t dense_mask;               // bit l set if level l is dense
@@ -126,6 +127,7 @@ struct nr_subject {
   // derived, rebuilt when parameters change
   __half2 *table16 = nullptr;
   float *blob = nullptr;
+  float4 *wquad = nullptr;           // corner-block copy of the bone channels of wvol
   nr::BlobLayout lay{};
   __nv_bfloat16 *tc_bf16 = nullptr;
   __half *tc_f16 = nullptr;

@@ -14,45 +14,35 @@ namespace nr {
 // i of the canonical weight volume (vertices on the box corners, a corner
 // outside the grid contributes zero).  The denominator S is floored at kEpsW.
 
-__device__ __forceinline__ float vol_fetch(const float *__restrict__ ch, int i) { return __ldg(ch + i); }
-
-// Trilinear sample of one channel at grid coordinate u (in vertex units).
-__device__ __forceinline__ float trilinear_channel(const float *__restrict__ ch, int R, float ux, float uy,
-                                                   float uz) {
+// Trilinear sample of one bone channel through its corner-block copy: entry
+// (z, y, x), z in [-1, R], y and x in [-1, R-1], holds the float4
+// (V[z][y][x], V[z][y][x+1], V[z][y+1][x], V[z][y+1][x+1]) with V = 0 outside the
+// grid, so a point whose cell origin lies in [-1, R-1]^3 needs exactly two
+// aligned 16-byte loads (z and z + 1); any other point is farther than one
+// cell from the grid and reads zero.
+__device__ __forceinline__ float trilinear_quad(const float4 *__restrict__ q, int R, float ux, float uy, float uz) {
   const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
   const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
-  const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
-  if (ix >= 0 && iy >= 0 && iz >= 0 && ix + 1 < R && iy + 1 < R && iz + 1 < R) {
-    const int b = (iz * R + iy) * R + ix;
-    const int RR = R * R;
-    const float c000 = vol_fetch(ch, b), c100 = vol_fetch(ch, b + 1);
-    const float c010 = vol_fetch(ch, b + R), c110 = vol_fetch(ch, b + R + 1);
-    const float c001 = vol_fetch(ch, b + RR), c101 = vol_fetch(ch, b + RR + 1);
-    const float c011 = vol_fetch(ch, b + RR + R), c111 = vol_fetch(ch, b + RR + R + 1);
-    const float c00 = fmaf(fx, c100 - c000, c000), c10 = fmaf(fx, c110 - c010, c010);
-    const float c01 = fmaf(fx, c101 - c001, c001), c11 = fmaf(fx, c111 - c011, c011);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0);
-  }
   if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) return 0.f;
-  float acc = 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int ax = ix + (c & 1), ay = iy + ((c >> 1) & 1), az = iz + (c >> 2);
-    if (ax < 0 || ay < 0 || az < 0 || ax >= R || ay >= R || az >= R) continue;
-    const float w = ((c & 1) ? fx : 1.f - fx) * (((c >> 1) & 1) ? fy : 1.f - fy) * ((c >> 2) ? fz : 1.f - fz);
-    acc = fmaf(w, vol_fetch(ch, (az * R + ay) * R + ax), acc);
-  }
-  return acc;
+  const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
+  const int R1 = R + 1;
+  const int b = ((iz + 1) * R1 + (iy + 1)) * R1 + (ix + 1);
+  const float4 a = __ldg(q + b), c = __ldg(q + b + R1 * R1);
+  const float a0 = fmaf(fx, a.y - a.x, a.x), a1 = fmaf(fx, a.w - a.z, a.z);
+  const float c0 = fmaf(fx, c.y - c.x, c.x), c1 = fmaf(fx, c.w - c.z, c.z);
+  const float z0 = fmaf(fy, a1 - a0, a0), z1 = fmaf(fy, c1 - c0, c0);
+  return fmaf(fz, z1 - z0, z0);
 }
+
+__host__ __device__ inline size_t quad_channel(int R) { return (size_t)(R + 2) * (R + 1) * (R + 1); }
 
 // sG: the 24 bone transforms [24][12] (rows [R | t]) in shared memory.
 __device__ __forceinline__ void lbs_warp(const FieldParams &P, const float *__restrict__ sG, float x0, float x1,
                                          float x2, float &s0, float &s1, float &s2, float &S) {
   const int R = P.wres;
-  const int R3 = R * R * R;
+  const size_t QC = quad_channel(R);
   float n0 = 0.f, n1 = 0.f, n2 = 0.f, sum = 0.f;
-#pragma unroll 2
+#pragma unroll 4
   for (int i = 0; i < kBones; ++i) {
     const float *g = sG + 12 * i;
     const float p0 = fmaf(g[0], x0, fmaf(g[1], x1, fmaf(g[2], x2, g[3])));
@@ -61,7 +51,7 @@ __device__ __forceinline__ void lbs_warp(const FieldParams &P, const float *__re
     const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
     const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
     const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
-    const float w = trilinear_channel(P.wvol + (size_t)i * R3, R, ux, uy, uz);
+    const float w = trilinear_quad(P.wquad + (size_t)i * QC, R, ux, uy, uz);
     sum += w;
     n0 = fmaf(w, p0, n0);
     n1 = fmaf(w, p1, n1);

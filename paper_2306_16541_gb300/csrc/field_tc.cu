@@ -16,7 +16,7 @@
 
 namespace nr {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kGamRow = kResGammaPad + 8;   // 56: gamma tile row stride (elements)
 constexpr int kEncRow = kMlpIn + 8;         // 40: encoding tile row stride (elements)
@@ -68,87 +68,77 @@ __device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
-// A fragments of a 32 x (16 KT) row-major tile (two m16 tiles) from shared memory.
+// The MLP phase runs one 16-row m-tile of the warp's 32 samples at a time, so
+// only one tile's accumulators (32 floats) and A fragments (16 registers) are
+// live; the two tiles reuse the same weight fragments from shared memory.
+
+// A fragments of rows m0 .. m0+15 of a row-major [32][lda] tile, K = 16 KT.
 template <int KT, typename T>
-__device__ __forceinline__ void load_a(const T *A, int lda, uint32_t (&a)[2][KT][4]) {
+__device__ __forceinline__ void load_a(const T *A, int lda, int m0, uint32_t (&a)[KT][4]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) ldsm_x4(a[mt][kt], A + (mt * 16 + (lane & 15)) * lda + kt * 16 + (lane >> 4) * 8);
+  for (int kt = 0; kt < KT; ++kt) ldsm_x4(a[kt], A + (m0 + (lane & 15)) * lda + kt * 16 + (lane >> 4) * 8);
 }
 
-// acc[mt][nt] initialised with the bias of columns nt*8 + 2t, +1.
+// acc[nt] initialised with the bias of columns nt*8 + 2t, +1.
 template <int NT>
-__device__ __forceinline__ void init_bias(const float *bias, float (&acc)[2][NT][4]) {
+__device__ __forceinline__ void init_bias(const float *bias, float (&acc)[NT][4]) {
   const int t = threadIdx.x & 3;
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) {
     const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      acc[mt][nt][0] = b0;
-      acc[mt][nt][1] = b1;
-      acc[mt][nt][2] = b0;
-      acc[mt][nt][3] = b1;
-    }
+    acc[nt][0] = b0;
+    acc[nt][1] = b1;
+    acc[nt][2] = b0;
+    acc[nt][3] = b1;
   }
 }
 
-// acc += A[32 x 16KT] * W^T, W row-major [8NT][ldw] (rows = outputs), columns k0 .. k0 + 16KT.
+// acc += A[16 x 16KT] * W^T, W row-major [8NT][ldw] (rows = outputs), columns k0 .. k0 + 16KT.
 template <typename T, int KT, int NT>
-__device__ __forceinline__ void mma_block(const uint32_t (&a)[2][KT][4], const T *W, int ldw, int k0,
-                                          float (&acc)[2][NT][4]) {
+__device__ __forceinline__ void mma_block(const uint32_t (&a)[KT][4], const T *W, int ldw, int k0,
+                                          float (&acc)[NT][4]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int kt = 0; kt < KT; ++kt) {
     if constexpr (NT == 1) {
       uint32_t b0, b1;
       ldsm_x2(b0, b1, W + (lane & 7) * ldw + k0 + kt * 16 + ((lane >> 3) & 1) * 8);
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) TcOps<T>::mma(acc[mt][0], a[mt][kt], b0, b1);
+      TcOps<T>::mma(acc[0], a[kt], b0, b1);
     } else {
 #pragma unroll
       for (int np = 0; np < NT / 2; ++np) {
         uint32_t b[4];
         const int m = lane >> 3, r = lane & 7;
         ldsm_x4(b, W + (np * 16 + (m >> 1) * 8 + r) * ldw + k0 + kt * 16 + (m & 1) * 8);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          TcOps<T>::mma(acc[mt][2 * np], a[mt][kt], b[0], b[1]);
-          TcOps<T>::mma(acc[mt][2 * np + 1], a[mt][kt], b[2], b[3]);
-        }
+        TcOps<T>::mma(acc[2 * np], a[kt], b[0], b[1]);
+        TcOps<T>::mma(acc[2 * np + 1], a[kt], b[2], b[3]);
       }
     }
   }
 }
 
-// ReLU of a 32 x 64 accumulator block, re-packed as the A operand (K = 64) of the next layer.
+// ReLU of a 16 x 64 accumulator block, re-packed as the A operand (K = 64) of the next layer.
 template <typename T>
-__device__ __forceinline__ void relu_to_a(const float (&acc)[2][8][4], uint32_t (&a)[2][4][4]) {
+__device__ __forceinline__ void relu_to_a(const float (&acc)[8][4], uint32_t (&a)[4][4]) {
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float *c0 = acc[mt][2 * j], *c1 = acc[mt][2 * j + 1];
-      a[mt][j][0] = TcOps<T>::pack(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
-      a[mt][j][1] = TcOps<T>::pack(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
-      a[mt][j][2] = TcOps<T>::pack(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
-      a[mt][j][3] = TcOps<T>::pack(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
-    }
+  for (int j = 0; j < 4; ++j) {
+    const float *c0 = acc[2 * j], *c1 = acc[2 * j + 1];
+    a[j][0] = TcOps<T>::pack(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
+    a[j][1] = TcOps<T>::pack(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
+    a[j][2] = TcOps<T>::pack(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
+    a[j][3] = TcOps<T>::pack(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
+  }
 }
 
-// Writes columns 0..3 of a 32 x 8 accumulator block to out[32][4] (float).
-__device__ __forceinline__ void store_out4(const float (&acc)[2][1][4], float *out) {
+// Writes columns 0..3 of a 16 x 8 accumulator block to rows m0.. of out[32][4] (float).
+__device__ __forceinline__ void store_out4(const float (&acc)[1][4], int m0, float *out) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   if (t < 2) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      out[(mt * 16 + g) * 4 + 2 * t] = acc[mt][0][0];
-      out[(mt * 16 + g) * 4 + 2 * t + 1] = acc[mt][0][1];
-      out[(mt * 16 + g + 8) * 4 + 2 * t] = acc[mt][0][2];
-      out[(mt * 16 + g + 8) * 4 + 2 * t + 1] = acc[mt][0][3];
-    }
+    out[(m0 + g) * 4 + 2 * t] = acc[0][0];
+    out[(m0 + g) * 4 + 2 * t + 1] = acc[0][1];
+    out[(m0 + g + 8) * 4 + 2 * t] = acc[0][2];
+    out[(m0 + g + 8) * 4 + 2 * t + 1] = acc[0][3];
   }
 }
 
@@ -181,9 +171,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
   float *sBias = reinterpret_cast<float *>(smem + ((P.tlay.total * sizeof(T) + 15) & ~size_t(15)));
   const TcBias bl = tc_bias_layout(P.hidden);
   float *sG = sBias + ((bl.total + 3) & ~3);
+  // per warp: one [32][kGamRow] tile that holds gamma(x_skel) for the residual MLP and,
+  // once that is done, the hash encoding (row stride kEncRow) for the canonical MLP
   T *sGam = reinterpret_cast<T *>(sG + kBones * 12);                     // [warps][32][kGamRow]
-  T *sEnc = sGam + kTcWarps * 32 * kGamRow;                              // [warps][32][kEncRow]
-  float *sOut = reinterpret_cast<float *>(sEnc + kTcWarps * 32 * kEncRow);  // [warps][32][4]
+  float *sOut = reinterpret_cast<float *>(sGam + kTcWarps * 32 * kGamRow);  // [warps][32][4]
 
   {  // stage weights, biases and the pose's bone transforms
     const int4 *src = reinterpret_cast<const int4 *>(P.tc_blob);
@@ -199,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
     copyb(bl.r4, P.blob + P.lay.r4b, kWidth, kWidth);
     copyb(bl.r5, P.blob + P.lay.r5b, 3, 8);
     copyb(bl.c0, P.blob + P.lay.c0b, kWidth, kWidth);
-    for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.ch[l], P.blob + P.lay.chb[l], kWidth, kWidth);
+    for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.c0 + kWidth * (l + 1), P.blob + P.lay.chb[l], kWidth, kWidth);
     copyb(bl.cl, P.blob + P.lay.clb, 4, 8);
     for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
   }
@@ -207,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T *gam = sGam + warp * 32 * kGamRow;
-  T *enc = sEnc + warp * 32 * kEncRow;
+  T *enc = gam;
   float *o4 = sOut + warp * 32 * 4;
   const uint32_t n = n_dev ? *n_dev : n_fixed;
   const uint32_t n_tiles = (n + 31) / 32;
@@ -263,26 +254,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
         for (int k = 0; k < kResGammaPad / 2; ++k) row[k] = TcOps<T>::pack(g[2 * k], g[2 * k + 1]);
       }
       __syncwarp();
-      uint32_t ag[2][3][4], a[2][4][4];
-      float acc[2][8][4];
-      load_a<3>(gam, kGamRow, ag);
-      init_bias(sBias + bl.r1, acc);
-      mma_block<T, 3, 8>(ag, sW + P.tlay.r1, kTcRow, 0, acc);
-      relu_to_a<T>(acc, a);
-      init_bias(sBias + bl.r2, acc);
-      mma_block<T, 4, 8>(a, sW + P.tlay.r2, kTcRow, 0, acc);
-      relu_to_a<T>(acc, a);
-      init_bias(sBias + bl.r3, acc);
-      mma_block<T, 4, 8>(a, sW + P.tlay.r3, kTcRow, 0, acc);
-      relu_to_a<T>(acc, a);
-      init_bias(sBias + bl.r4, acc);                               // layer 4 sees [h3, gamma]
-      mma_block<T, 4, 8>(a, sW + P.tlay.r4, kTcRowWide, 0, acc);
-      mma_block<T, 3, 8>(ag, sW + P.tlay.r4, kTcRowWide, kWidth, acc);
-      relu_to_a<T>(acc, a);
-      float acc5[2][1][4];
-      init_bias(sBias + bl.r5, acc5);
-      mma_block<T, 4, 1>(a, sW + P.tlay.r5, kTcRow, 0, acc5);
-      store_out4(acc5, o4);
+#pragma unroll 1
+      for (int m0 = 0; m0 < 32; m0 += 16) {
+        uint32_t ag[3][4], a[4][4];
+        float acc[8][4];
+        load_a<3>(gam, kGamRow, m0, ag);
+        init_bias(sBias + bl.r1, acc);
+        mma_block<T, 3, 8>(ag, sW + P.tlay.r1, kTcRow, 0, acc);
+        relu_to_a<T>(acc, a);
+        init_bias(sBias + bl.r2, acc);
+        mma_block<T, 4, 8>(a, sW + P.tlay.r2, kTcRow, 0, acc);
+        relu_to_a<T>(acc, a);
+        init_bias(sBias + bl.r3, acc);
+        mma_block<T, 4, 8>(a, sW + P.tlay.r3, kTcRow, 0, acc);
+        relu_to_a<T>(acc, a);
+        init_bias(sBias + bl.r4, acc);                               // layer 4 sees [h3, gamma]
+        mma_block<T, 4, 8>(a, sW + P.tlay.r4, kTcRowWide, 0, acc);
+        mma_block<T, 3, 8>(ag, sW + P.tlay.r4, kTcRowWide, kWidth, acc);
+        relu_to_a<T>(acc, a);
+        float acc5[1][4];
+        init_bias(sBias + bl.r5, acc5);
+        mma_block<T, 4, 1>(a, sW + P.tlay.r5, kTcRow, 0, acc5);
+        store_out4(acc5, m0, o4);
+      }
       __syncwarp();
       f0 += o4[lane * 4 + 0];
       f1 += o4[lane * 4 + 1];
@@ -317,22 +311,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
       }
     }
     __syncwarp();
-    {
-      uint32_t ae[2][2][4], a[2][4][4];
-      float acc[2][8][4];
-      load_a<2>(enc, kEncRow, ae);
+#pragma unroll 1
+    for (int m0 = 0; m0 < 32; m0 += 16) {
+      uint32_t ae[2][4], a[4][4];
+      float acc[8][4];
+      load_a<2>(enc, kEncRow, m0, ae);
       init_bias(sBias + bl.c0, acc);
       mma_block<T, 2, 8>(ae, sW + P.tlay.c0, kTcRow, 0, acc);
       relu_to_a<T>(acc, a);
       for (int l = 0; l < P.hidden - 1; ++l) {
-        init_bias(sBias + bl.ch[l], acc);
+        init_bias(sBias + bl.c0 + kWidth * (l + 1), acc);
         mma_block<T, 4, 8>(a, sW + P.tlay.ch[l], kTcRow, 0, acc);
         relu_to_a<T>(acc, a);
       }
-      float acco[2][1][4];
+      float acco[1][4];
       init_bias(sBias + bl.cl, acco);
       mma_block<T, 4, 1>(a, sW + P.tlay.cl, kTcRow, 0, acco);
-      store_out4(acco, o4);
+      store_out4(acco, m0, o4);
     }
     __syncwarp();
     if (valid) {
@@ -357,7 +352,7 @@ static size_t tc_smem(const FieldParams &P) {
   const TcBias bl = tc_bias_layout(P.hidden);
   size_t b = ((P.tlay.total * sizeof(T) + 15) & ~size_t(15));
   b += sizeof(float) * (((bl.total + 3) & ~3) + kBones * 12);
-  b += sizeof(T) * (size_t)kTcWarps * 32 * (kGamRow + kEncRow);
+  b += sizeof(T) * (size_t)kTcWarps * 32 * kGamRow;
   b += sizeof(float) * (size_t)kTcWarps * 32 * 4;
   return b;
 }

@@ -8,7 +8,7 @@
 #include <atomic>
 #include <new>
 
-#include "common.cuh"
+#include "field.cuh"
 
 namespace nr {
 
@@ -179,6 +179,26 @@ __global__ void pack_tc_kernel(const float *__restrict__ W, int src_stride, int 
   const int j = i / in_pad, k = i % in_pad;
   const float v = (k < n_in && j < out) ? W[(size_t)j * src_stride + col0 + k] : 0.f;
   dst[(size_t)j * row_stride + dcol0 + k] = T(v);
+}
+
+// Corner-block copy of the bone channels (see trilinear_quad in field.cuh).
+__global__ void build_quad_kernel(const float *__restrict__ vol, int R, float4 *__restrict__ quad) {
+  const size_t QC = quad_channel(R);
+  const size_t n = QC * kBones;
+  const int R1 = R + 1;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / QC);
+    size_t r = e % QC;
+    const int x = (int)(r % R1) - 1;
+    r /= R1;
+    const int y = (int)(r % R1) - 1;
+    const int z = (int)(r / R1) - 1;
+    const float *ch = vol + (size_t)c * R * R * R;
+    auto at = [&](int zz, int yy, int xx) -> float {
+      return (zz < 0 || yy < 0 || xx < 0 || zz >= R || yy >= R || xx >= R) ? 0.f : ch[((size_t)zz * R + yy) * R + xx];
+    };
+    quad[e] = make_float4(at(z, y, x), at(z, y, x + 1), at(z, y + 1, x), at(z, y + 1, x + 1));
+  }
 }
 
 __global__ void copy_kernel(const float *__restrict__ src, int n, float *__restrict__ dst) {
@@ -363,8 +383,10 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   // tensor-core copies
   launched += pack_tc_all<__nv_bfloat16>(s, m, st, s->tc_bf16);
   launched += pack_tc_all<__half>(s, m, st, s->tc_f16);
-  // half-precision hash table
+  // half-precision hash table, corner-block weight volume
   table_to_f16_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->table), s->n_table / 2, s->table16);
+  build_quad_kernel<<<2048, 256, 0, st>>>(s->wvol, (int)s->wres, s->wquad);
+  launched += 1;
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(launched + 1);
   s->params_dirty = false;
@@ -419,6 +441,7 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   }
   P.wres = (int)s->wres;
   P.wvol = s->wvol;
+  P.wquad = s->wquad;
   P.L = (int)s->L;
   P.T_mask = s->T - 1;
   for (uint32_t l = 0; l < s->L; ++l) {
@@ -458,7 +481,7 @@ extern "C" const char *nr_last_error(void) { return nr::g_err; }
 extern "C" uint64_t nr_launch_count(void) { return nr::g_launches.load(std::memory_order_relaxed); }
 
 static void free_subject(nr_subject *s) {
-  void *bufs[] = {s->wvol,   s->g_wvol,  s->table,    s->g_table,  s->mlp,       s->g_mlp,     s->res,
+  void *bufs[] = {s->wquad,  s->wvol,   s->g_wvol,  s->table,    s->g_table,  s->mlp,       s->g_mlp,     s->res,
                   s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->blob,      s->tc_bf16,   s->tc_f16,
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
@@ -551,6 +574,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->g_res, s->n_res * 4);
   ALLOC(s->table16, s->n_table * 2);
   ALLOC(s->blob, (size_t)s->lay.total * 4);
+  ALLOC(s->wquad, quad_channel((int)s->wres) * kBones * sizeof(float4));
   ALLOC(s->tc_bf16, (size_t)s->tlay.total * 2);
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
   ALLOC(s->d_G, kBones * 12 * 4);
