@@ -143,7 +143,9 @@ typedef struct {
 } nr_camera;
 
 typedef struct {
-  nr_dtype mlp_dtype;      /* NR_F32 (CUDA cores), NR_BF16, NR_F16 (tensor cores) */
+  nr_dtype mlp_dtype;      /* NR_F32 (CUDA cores), NR_BF16, NR_F16, NR_FP8E4M3 (tensor cores;
+                              e4m3 uses per-matrix weight scales and static per-subject
+                              activation scales calibrated once on a seeded probe) */
   nr_dtype feat_dtype;     /* hash-table storage read by the encoder: NR_F32 or NR_F16 */
   uint32_t use_occupancy;  /* skip samples whose posed occupancy cell is empty */
   float t_min;             /* early ray termination once transmittance < t_min; 0 = off */

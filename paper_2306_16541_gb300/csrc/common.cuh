@@ -88,6 +88,8 @@ struct FieldParams {
   TcLayout tlay;
   const float *G;                    // [24][12] of the current pose
   const float *bias1;                // [64] residual layer-1 bias with the pose folded in
+  const uint8_t *fp8_blob;           // e4m3 weight blob (field_fp8.cu)
+  const float *fp8_scales;           // its weight and activation scales
 };
 
 struct Frame {                       // a training frame's camera (decoded)
@@ -133,6 +135,11 @@ struct nr_subject {
   __half *tc_f16 = nullptr;
   nr::TcLayout tlay{};
   bool params_dirty = true;
+  uint8_t *fp8_blob = nullptr;       // e4m3 weights, their scales, calibration buffers
+  float *fp8_scales = nullptr;
+  void *fp8_jobs = nullptr;
+  float *fp8_G = nullptr;
+  bool fp8_ready = false;
   // current pose
   bool pose_set = false;
   float h_G[24 * 12];
@@ -194,6 +201,7 @@ nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *b
 bool subject_ok(const nr_subject *s);
 nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs
 nr_status ensure_bias(nr_subject *s, cudaStream_t st);         // pose-folded bias
+nr_status prepare_fp8(nr_subject *s, cudaStream_t st);         // e4m3 weights + calibrated scales
 FieldParams field_params(const nr_subject *s, const nr_render_opts *o);
 nr_status set_error_cuda(cudaError_t e, const char *what);
 }  // namespace nr

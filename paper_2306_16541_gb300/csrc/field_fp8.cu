@@ -1,0 +1,537 @@
+// field_fp8.cu -- the per-sample field with both MLPs in FP8 E4M3 on the
+// tensor cores (mma.sync m16n8k32, float32 accumulation) and per-layer scaling.
+//
+// Scaling: every weight matrix W is stored as e4m3(W / s_w) with
+// s_w = max|W| / 448; every layer input x as e4m3(x / s_a) with a static
+// per-subject scale s_a = amax(x) / 448, amax measured once on a seeded probe
+// of 65,536 points spread over the box at the rest pose (float32 path), with a
+// 2x margin.  A layer computes y = (s_w s_a) (W_q x_q) + b in float32; the
+// residual's fourth layer sums its h3 and gamma blocks with their own scales.
+// The scales are fixed per subject (recomputed only when its parameters change),
+// so a sample's result does not depend on what else is in the batch.
+//
+// Structure follows field_tc.cu (one warp per 32 samples, float32 gathers one
+// sample per lane, MLPs on 16-row tiles); between layers the accumulators are
+// requantised to e4m3 through a per-warp shared-memory tile.
+#include "field.cuh"
+#include "mma.cuh"
+#include "render.cuh"
+
+namespace nr {
+
+constexpr int kF8Threads = 512;
+constexpr int kF8Warps = kF8Threads / 32;
+constexpr int kF8Row = 80;     // bytes per row of a K = 64 operand (64 + 16 pad)
+constexpr int kF8Row32 = 48;   // bytes per row of a K = 32 operand (32 + 16 pad)
+constexpr float kE4M3Max = 448.f;
+
+// Byte offsets of the e4m3 weight blob; matrices are [out][in] rows.
+struct Fp8Layout {
+  int r1, r2, r3, r4h, r4g, r5, c0, ch[kMaxHidden], cl, total;
+};
+
+// Scale slots (floats): weight scales, then activation (layer-input) scales.
+enum {
+  SW_R1, SW_R2, SW_R3, SW_R4H, SW_R4G, SW_R5, SW_C0, SW_CH0, SW_CL = SW_CH0 + kMaxHidden,
+  SA_GAM, SA_RH1, SA_RH2, SA_RH3, SA_RH4, SA_ENC, SA_CH1, kFp8Scales = SA_CH1 + kMaxHidden
+};
+
+__host__ __device__ inline Fp8Layout fp8_layout(int hidden) {
+  Fp8Layout f{};
+  int o = 0;
+  f.r1 = o; o += kWidth * kF8Row;
+  f.r2 = o; o += kWidth * kF8Row;
+  f.r3 = o; o += kWidth * kF8Row;
+  f.r4h = o; o += kWidth * kF8Row;
+  f.r4g = o; o += kWidth * kF8Row;
+  f.r5 = o; o += 8 * kF8Row;
+  f.c0 = o; o += kWidth * kF8Row32;
+  for (int l = 0; l < hidden - 1; ++l) { f.ch[l] = o; o += kWidth * kF8Row; }
+  f.cl = o; o += 8 * kF8Row;
+  f.total = o;
+  return f;
+}
+
+__device__ __forceinline__ void mma_e4m3(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint16_t to_e4m3x2(float lo, float hi) {
+  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// A fragments (K = 32 KT bytes) of rows m0..m0+15 of a byte tile with row stride `ld`.
+template <int KT>
+__device__ __forceinline__ void load_a8(const uint8_t *A, int ld, int m0, uint32_t (&a)[KT][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt) ldsm_x4(a[kt], A + (m0 + (lane & 15)) * ld + kt * 32 + (lane >> 4) * 16);
+}
+
+// acc += A * W^T for W [8NT][ld] e4m3 rows.
+template <int KT, int NT>
+__device__ __forceinline__ void mma8(const uint32_t (&a)[KT][4], const uint8_t *W, int ld, float (&acc)[NT][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt) {
+    if constexpr (NT == 1) {
+      uint32_t b0, b1;
+      ldsm_x2(b0, b1, W + (lane & 7) * ld + kt * 32 + ((lane >> 3) & 1) * 16);
+      mma_e4m3(acc[0], a[kt], b0, b1);
+    } else {
+#pragma unroll
+      for (int np = 0; np < NT / 2; ++np) {
+        uint32_t b[4];
+        const int m = lane >> 3, r = lane & 7;
+        ldsm_x4(b, W + (np * 16 + (m >> 1) * 8 + r) * ld + kt * 32 + (m & 1) * 16);
+        mma_e4m3(acc[2 * np], a[kt], b[0], b[1]);
+        mma_e4m3(acc[2 * np + 1], a[kt], b[2], b[3]);
+      }
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void zero_acc(float (&acc)[NT][4]) {
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+}
+
+// y = relu(mult * acc + bias) requantised with 1 / s_next into rows m0.. of a [32][kF8Row] tile.
+__device__ __forceinline__ void epilogue_store(const float (&acc)[8][4], float mult, const float *bias,
+                                               float inv_next, uint8_t *tile, int m0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
+    const float y0 = fmaxf(fmaf(mult, acc[nt][0], b0), 0.f) * inv_next;
+    const float y1 = fmaxf(fmaf(mult, acc[nt][1], b1), 0.f) * inv_next;
+    const float y2 = fmaxf(fmaf(mult, acc[nt][2], b0), 0.f) * inv_next;
+    const float y3 = fmaxf(fmaf(mult, acc[nt][3], b1), 0.f) * inv_next;
+    *reinterpret_cast<uint16_t *>(tile + (m0 + g) * kF8Row + nt * 8 + 2 * t) = to_e4m3x2(y0, y1);
+    *reinterpret_cast<uint16_t *>(tile + (m0 + g + 8) * kF8Row + nt * 8 + 2 * t) = to_e4m3x2(y2, y3);
+  }
+}
+
+// acc = mult * acc + mult2 * acc2 (the two K blocks of the residual's fourth layer).
+__device__ __forceinline__ void combine(float (&acc)[8][4], float mult, const float (&acc2)[8][4], float mult2) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = fmaf(mult, acc[nt][q], mult2 * acc2[nt][q]);
+}
+
+// Columns 0..3 of mult * acc + bias (a 16 x 8 block) into rows m0.. of out[32][4].
+__device__ __forceinline__ void store_out4s(const float (&acc)[1][4], float mult, const float *bias, int m0,
+                                            float *out) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  if (t < 2) {
+    const float b0 = bias[2 * t], b1 = bias[2 * t + 1];
+    out[(m0 + g) * 4 + 2 * t] = fmaf(mult, acc[0][0], b0);
+    out[(m0 + g) * 4 + 2 * t + 1] = fmaf(mult, acc[0][1], b1);
+    out[(m0 + g + 8) * 4 + 2 * t] = fmaf(mult, acc[0][2], b0);
+    out[(m0 + g + 8) * 4 + 2 * t + 1] = fmaf(mult, acc[0][3], b1);
+  }
+}
+
+struct Fp8Params {
+  const uint8_t *blob;
+  const float *scales;        // [kFp8Scales]
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kF8Threads, 1) field_fp8_kernel(FieldParams P, Fp8Params Q, const float4 *__restrict__ in,
+                                                                  uint32_t n_fixed, const uint32_t *__restrict__ n_dev,
+                                                                  float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Fp8Layout fl = fp8_layout(P.hidden);
+  const TcBias bl = tc_bias_layout(P.hidden);
+  uint8_t *sW = smem;
+  float *sBias = reinterpret_cast<float *>(smem + ((fl.total + 15) & ~15));
+  float *sS = sBias + ((bl.total + 3) & ~3);                              // scales
+  float *sG = sS + ((kFp8Scales + 3) & ~3);
+  uint8_t *sGam = reinterpret_cast<uint8_t *>(sG + kBones * 12);           // [warps][32][kF8Row]
+  uint8_t *sH = sGam + kF8Warps * 32 * kF8Row;                             // [warps][32][kF8Row]
+  float *sOut = reinterpret_cast<float *>(sH + kF8Warps * 32 * kF8Row);   // [warps][32][4]
+  {
+    const int4 *src = reinterpret_cast<const int4 *>(Q.blob);
+    int4 *dst = reinterpret_cast<int4 *>(sW);
+    for (int i = threadIdx.x; i < fl.total / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    auto copyb = [&](int dsto, const float *s, int n, int npad) {
+      for (int i = threadIdx.x; i < npad; i += blockDim.x) sBias[dsto + i] = i < n ? s[i] : 0.f;
+    };
+    copyb(bl.r1, P.bias1, kWidth, kWidth);
+    copyb(bl.r2, P.blob + P.lay.r2b, kWidth, kWidth);
+    copyb(bl.r3, P.blob + P.lay.r3b, kWidth, kWidth);
+    copyb(bl.r4, P.blob + P.lay.r4b, kWidth, kWidth);
+    copyb(bl.r5, P.blob + P.lay.r5b, 3, 8);
+    copyb(bl.c0, P.blob + P.lay.c0b, kWidth, kWidth);
+    for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.c0 + kWidth * (l + 1), P.blob + P.lay.chb[l], kWidth, kWidth);
+    copyb(bl.cl, P.blob + P.lay.clb, 4, 8);
+    for (int i = threadIdx.x; i < kFp8Scales; i += blockDim.x) sS[i] = Q.scales[i];
+    for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t *gam = sGam + warp * 32 * kF8Row;
+  uint8_t *hh = sH + warp * 32 * kF8Row;
+  float *o4 = sOut + warp * 32 * 4;
+  const uint32_t n = n_dev ? *n_dev : n_fixed;
+  const uint32_t n_tiles = (n + 31) / 32;
+  for (uint32_t tile = blockIdx.x * kF8Warps + warp; tile < n_tiles; tile += gridDim.x * kF8Warps) {
+    const uint32_t j = tile * 32 + lane;
+    const bool valid = j < n;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f, delta = 0.f;
+    if (valid) {
+      if (MODE == kModeRender) {
+        const float4 s = in[j];
+        x0 = s.x; x1 = s.y; x2 = s.z; delta = s.w;
+      } else {
+        const float *q = reinterpret_cast<const float *>(in) + 3 * (size_t)j;
+        x0 = q[0]; x1 = q[1]; x2 = q[2];
+      }
+    }
+    float s0, s1, s2, S;
+    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
+    float f0 = s0, f1 = s1, f2 = s2;
+    if (P.res_enabled) {
+      {  // gamma(x_skel) quantised with 1 / s_gamma into the lane's row (48 values, zero to 64)
+        const float ig = 1.f / sS[SA_GAM];
+        const float h[3] = {(s0 - P.box_c[0]) * P.box_ih[0], (s1 - P.box_c[1]) * P.box_ih[1],
+                            (s2 - P.box_c[2]) * P.box_ih[2]};
+        uint8_t *row = gam + lane * kF8Row;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) row[a] = to_e4m3(h[a] * ig);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float sc = (float)(1 << k);
+          const float w = (k < P.res_freqs) ? P.hann[k] : 0.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float sn, cs;
+            sincospif(sc * h[a], &sn, &cs);
+            row[3 + 6 * k + a] = to_e4m3(w * sn * ig);
+            row[6 + 6 * k + a] = to_e4m3(w * cs * ig);
+          }
+        }
+#pragma unroll
+        for (int k = 39; k < 64; ++k) row[k] = 0;
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int m0 = 0; m0 < 32; m0 += 16) {
+        uint32_t ag[2][4], a[2][4];
+        float acc[8][4], acc2[8][4];
+        load_a8<2>(gam, kF8Row, m0, ag);
+        zero_acc(acc);
+        mma8<2, 8>(ag, sW + fl.r1, kF8Row, acc);
+        epilogue_store(acc, sS[SW_R1] * sS[SA_GAM], sBias + bl.r1, 1.f / sS[SA_RH1], hh, m0);
+        __syncwarp();
+        load_a8<2>(hh, kF8Row, m0, a);
+        zero_acc(acc);
+        mma8<2, 8>(a, sW + fl.r2, kF8Row, acc);
+        __syncwarp();
+        epilogue_store(acc, sS[SW_R2] * sS[SA_RH1], sBias + bl.r2, 1.f / sS[SA_RH2], hh, m0);
+        __syncwarp();
+        load_a8<2>(hh, kF8Row, m0, a);
+        zero_acc(acc);
+        mma8<2, 8>(a, sW + fl.r3, kF8Row, acc);
+        __syncwarp();
+        epilogue_store(acc, sS[SW_R3] * sS[SA_RH2], sBias + bl.r3, 1.f / sS[SA_RH3], hh, m0);
+        __syncwarp();
+        load_a8<2>(hh, kF8Row, m0, a);                               // layer 4: [h3 | gamma]
+        zero_acc(acc);
+        zero_acc(acc2);
+        mma8<2, 8>(a, sW + fl.r4h, kF8Row, acc);
+        mma8<2, 8>(ag, sW + fl.r4g, kF8Row, acc2);
+        __syncwarp();
+        combine(acc, sS[SW_R4H] * sS[SA_RH3], acc2, sS[SW_R4G] * sS[SA_GAM]);
+        epilogue_store(acc, 1.f, sBias + bl.r4, 1.f / sS[SA_RH4], hh, m0);
+        __syncwarp();
+        load_a8<2>(hh, kF8Row, m0, a);
+        float acc5[1][4];
+        zero_acc(acc5);
+        mma8<2, 1>(a, sW + fl.r5, kF8Row, acc5);
+        store_out4s(acc5, sS[SW_R5] * sS[SA_RH4], sBias + bl.r5, m0, o4);
+      }
+      __syncwarp();
+      f0 += o4[lane * 4 + 0];
+      f1 += o4[lane * 4 + 1];
+      f2 += o4[lane * 4 + 2];
+      __syncwarp();
+    }
+    bool inside;
+    {  // hash encoding quantised with 1 / s_enc into the lane's row of the h tile (K = 32)
+      float p0 = (f0 - P.bmin[0]) * P.inv_box[0];
+      float p1 = (f1 - P.bmin[1]) * P.inv_box[1];
+      float p2 = (f2 - P.bmin[2]) * P.inv_box[2];
+      inside = p0 >= 0.f && p0 <= 1.f && p1 >= 0.f && p1 <= 1.f && p2 >= 0.f && p2 <= 1.f;
+      p0 = fminf(fmaxf(p0, 0.f), 1.f);
+      p1 = fminf(fmaxf(p1, 0.f), 1.f);
+      p2 = fminf(fmaxf(p2, 0.f), 1.f);
+      const float ie = 1.f / sS[SA_ENC];
+      uint16_t *row = reinterpret_cast<uint16_t *>(hh + lane * kF8Row);
+#pragma unroll
+      for (int l = 0; l < kMaxLevels; ++l) {
+        float fa = 0.f, fb = 0.f;
+        if (l < P.L) {
+          HashCell c;
+          hash_cell(P, l, p0, p1, p2, c);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float2 v = table_read(P, l, c.idx[k]);
+            fa = fmaf(c.w[k], v.x, fa);
+            fb = fmaf(c.w[k], v.y, fb);
+          }
+        }
+        row[l] = inside ? to_e4m3x2(fa * ie, fb * ie) : (uint16_t)0;
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int m0 = 0; m0 < 32; m0 += 16) {
+      uint32_t ae[1][4], a[2][4];
+      float acc[8][4];
+      load_a8<1>(hh, kF8Row, m0, ae);
+      zero_acc(acc);
+      mma8<1, 8>(ae, sW + fl.c0, kF8Row32, acc);
+      __syncwarp();
+      epilogue_store(acc, sS[SW_C0] * sS[SA_ENC], sBias + bl.c0, 1.f / sS[SA_CH1], hh, m0);
+      __syncwarp();
+      for (int l = 0; l < P.hidden - 1; ++l) {
+        load_a8<2>(hh, kF8Row, m0, a);
+        zero_acc(acc);
+        mma8<2, 8>(a, sW + fl.c0 + kWidth * kF8Row32 + l * kWidth * kF8Row, kF8Row, acc);
+        __syncwarp();
+        epilogue_store(acc, sS[SW_CH0 + l] * sS[SA_CH1 + l], sBias + bl.c0 + kWidth * (l + 1),
+                       1.f / sS[SA_CH1 + l + 1], hh, m0);
+        __syncwarp();
+      }
+      load_a8<2>(hh, kF8Row, m0, a);
+      float acco[1][4];
+      zero_acc(acco);
+      mma8<2, 1>(a, sW + fl.cl, kF8Row, acco);
+      store_out4s(acco, sS[SW_CL] * sS[SA_CH1 + P.hidden - 1], sBias + bl.cl, m0, o4);
+      __syncwarp();
+    }
+    __syncwarp();
+    if (valid) {
+      const float cr = sigmoidf_(o4[lane * 4 + 0]), cg = sigmoidf_(o4[lane * 4 + 1]);
+      const float cb = sigmoidf_(o4[lane * 4 + 2]), sigma = softplusf_(o4[lane * 4 + 3]);
+      if (MODE == kModeRender) {
+        const float al = inside ? (1.f - __expf(-sigma * delta)) * fminf(S, 1.f) : 0.f;
+        reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, al);
+      } else {
+        float *q = out + (size_t)NR_QUERY_STRIDE * j;
+        q[0] = s0; q[1] = s1; q[2] = s2; q[3] = S;
+        q[4] = f0; q[5] = f1; q[6] = f2; q[7] = inside ? 1.f : 0.f;
+        q[8] = cr; q[9] = cg; q[10] = cb; q[11] = sigma;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------- weight quantisation
+// One block per matrix: s_w = max|W| / 448, W_q = e4m3(W / s_w) into [out][ld] rows.
+struct QuantJob {
+  const float *W;      // packed master W[out][stride]
+  int stride, col0, n_in, out, out_pad, ld, dst, scale_slot;
+};
+
+__global__ void quantize_weights_kernel(const QuantJob *__restrict__ jobs, uint8_t *__restrict__ blob,
+                                        float *__restrict__ scales) {
+  const QuantJob J = jobs[blockIdx.x];
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < J.out * J.n_in; i += blockDim.x)
+    m = fmaxf(m, fabsf(J.W[(size_t)(i / J.n_in) * J.stride + J.col0 + i % J.n_in]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const float s = fmaxf(red[0], 1e-20f) / kE4M3Max;
+  if (threadIdx.x == 0) scales[J.scale_slot] = s;
+  for (int i = threadIdx.x; i < J.out_pad * J.ld; i += blockDim.x) {
+    const int r = i / J.ld, k = i % J.ld;
+    const float v = (r < J.out && k < J.n_in) ? J.W[(size_t)r * J.stride + J.col0 + k] / s : 0.f;
+    blob[J.dst + i] = to_e4m3(v);
+  }
+}
+
+// ------------------------------------------------------- activation calibration
+// The float32 field on 65,536 SplitMix64 points spread over the box at the rest
+// pose (identity transforms, zero joint angles); amax of every layer input, stored
+// as s_a = 2 amax / 448.
+constexpr int kCalThreads = 128;
+constexpr int kCalPoints = 65536;
+
+__device__ __forceinline__ void amax_to(float *dst, float v) {
+  atomicMax(reinterpret_cast<int *>(dst), __float_as_int(fabsf(v)));   // non-negative floats order as ints
+}
+
+__global__ void __launch_bounds__(kCalThreads) calibrate_kernel(FieldParams P, const float *__restrict__ bias_rest,
+                                                                float *__restrict__ amax) {
+  extern __shared__ float4 smem4[];
+  float *sW = reinterpret_cast<float *>(smem4);
+  float *sCol = sW + P.lay.total;
+  for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
+    reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
+  __syncthreads();
+  const int stride = blockDim.x;
+  float *hcol = sCol + threadIdx.x;
+  float *gcol = hcol + kWidth * stride;
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kCalPoints) return;
+  float x[3];
+  for (int k = 0; k < 3; ++k) {
+    uint64_t z = 0x5eedull + ((uint64_t)j * 3 + k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[k] = P.bmin[k] + (float)(z >> 40) * (1.f / 16777216.f) * (P.bmax[k] - P.bmin[k]);
+  }
+  float s0, s1, s2, S;
+  lbs_warp(P, P.G, x[0], x[1], x[2], s0, s1, s2, S);
+  float f0 = s0, f1 = s1, f2 = s2;
+  float y[kWidth];
+  float m = 0.f;
+  if (P.res_enabled) {
+    pos_enc(P, s0, s1, s2, gcol, stride);
+    for (int k = 0; k < kResGammaPad; ++k) m = fmaxf(m, fabsf(gcol[k * stride]));
+    amax_to(amax + SA_GAM, m);
+    dense_f32<kWidth>(sW + P.lay.r1, bias_rest, gcol, kResGammaPad, stride, y);
+    store_relu(y, hcol, stride);
+    const int rl[3] = {P.lay.r2, P.lay.r3, P.lay.r4};
+    const int rb[3] = {P.lay.r2b, P.lay.r3b, P.lay.r4b};
+    for (int l = 0; l < 3; ++l) {
+      m = 0.f;
+      for (int k = 0; k < kWidth; ++k) m = fmaxf(m, hcol[k * stride]);
+      amax_to(amax + SA_RH1 + l, m);
+      dense_f32<kWidth>(sW + rl[l], sW + rb[l], hcol, kWidth, stride, y);
+      if (l == 2) dense_acc_f32<kWidth>(sW + P.lay.r4 + kWidth * kWidth, gcol, kResGammaPad, stride, y);
+      store_relu(y, hcol, stride);
+    }
+    m = 0.f;
+    for (int k = 0; k < kWidth; ++k) m = fmaxf(m, hcol[k * stride]);
+    amax_to(amax + SA_RH4, m);
+    float o3[4];
+    dense_f32<4>(sW + P.lay.r5, sW + P.lay.r5b, hcol, kWidth, stride, o3);
+    f0 += o3[0];
+    f1 += o3[1];
+    f2 += o3[2];
+  }
+  hash_encode(P, f0, f1, f2, hcol, stride);
+  m = 0.f;
+  for (int k = 0; k < kMlpIn; ++k) m = fmaxf(m, fabsf(hcol[k * stride]));
+  amax_to(amax + SA_ENC, m);
+  dense_f32<kWidth>(sW + P.lay.c0, sW + P.lay.c0b, hcol, kMlpIn, stride, y);
+  store_relu(y, hcol, stride);
+  for (int l = 0; l < P.hidden; ++l) {
+    m = 0.f;
+    for (int k = 0; k < kWidth; ++k) m = fmaxf(m, hcol[k * stride]);
+    amax_to(amax + SA_CH1 + l, m);
+    if (l + 1 < P.hidden) {
+      dense_f32<kWidth>(sW + P.lay.ch[l], sW + P.lay.chb[l], hcol, kWidth, stride, y);
+      store_relu(y, hcol, stride);
+    }
+  }
+}
+
+__global__ void finish_scales_kernel(float *__restrict__ scales, int first, int count) {
+  const int i = threadIdx.x;
+  if (i < count) scales[first + i] = fmaxf(2.f * scales[first + i], 1e-20f) / kE4M3Max;
+}
+
+nr_status prepare_fp8(nr_subject *s, cudaStream_t st) {
+  if (s->fp8_ready) return NR_OK;
+  const Fp8Layout fl = fp8_layout((int)s->hidden);
+  if (!s->fp8_blob) {
+    NR_CHECK_CUDA(cudaMalloc(&s->fp8_blob, (size_t)fl.total));
+    NR_CHECK_CUDA(cudaMalloc(&s->fp8_scales, sizeof(float) * 64));
+    NR_CHECK_CUDA(cudaMalloc(&s->fp8_jobs, sizeof(QuantJob) * 16));
+    NR_CHECK_CUDA(cudaMalloc(&s->fp8_G, sizeof(float) * (kBones * 12 + kWidth)));
+  }
+  const MasterOffsets m = master_offsets(s);
+  const int g = res_gamma_dims(s), P3 = 3 * (int)s->K, H = (int)s->hidden;
+  std::vector<QuantJob> jobs;
+  auto add = [&](const float *W, int stride, int col0, int n_in, int out, int out_pad, int ld, int dst, int slot) {
+    jobs.push_back(QuantJob{W, stride, col0, n_in, out, out_pad, ld, dst, slot});
+  };
+  add(s->res + m.r[0], g + P3, 0, g, kWidth, kWidth, kF8Row, fl.r1, SW_R1);
+  add(s->res + m.r[1], kWidth, 0, kWidth, kWidth, kWidth, kF8Row, fl.r2, SW_R2);
+  add(s->res + m.r[2], kWidth, 0, kWidth, kWidth, kWidth, kF8Row, fl.r3, SW_R3);
+  add(s->res + m.r[3], kWidth + g, 0, kWidth, kWidth, kWidth, kF8Row, fl.r4h, SW_R4H);
+  add(s->res + m.r[3], kWidth + g, kWidth, g, kWidth, kWidth, kF8Row, fl.r4g, SW_R4G);
+  add(s->res + m.r[4], kWidth, 0, kWidth, 3, 8, kF8Row, fl.r5, SW_R5);
+  add(s->mlp + m.c[0], (int)s->mlp_in, 0, (int)s->mlp_in, kWidth, kWidth, kF8Row32, fl.c0, SW_C0);
+  for (int l = 1; l < H; ++l) add(s->mlp + m.c[l], kWidth, 0, kWidth, kWidth, kWidth, kF8Row, fl.ch[l - 1], SW_CH0 + l - 1);
+  add(s->mlp + m.c[H], kWidth, 0, kWidth, 4, 8, kF8Row, fl.cl, SW_CL);
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->fp8_jobs, jobs.data(), sizeof(QuantJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+  quantize_weights_kernel<<<(unsigned)jobs.size(), 256, 0, st>>>(reinterpret_cast<const QuantJob *>(s->fp8_jobs),
+                                                                  s->fp8_blob, s->fp8_scales);
+  // rest pose: identity transforms; folded bias b1 (zero joint angles)
+  std::vector<float> Gr(kBones * 12, 0.f);
+  for (int i = 0; i < kBones; ++i) Gr[12 * i] = Gr[12 * i + 5] = Gr[12 * i + 10] = 1.f;
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->fp8_G, Gr.data(), sizeof(float) * Gr.size(), cudaMemcpyHostToDevice, st));
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->fp8_G + kBones * 12, s->res + m.rb[0], sizeof(float) * kWidth,
+                                cudaMemcpyDeviceToDevice, st));
+  NR_CHECK_CUDA(cudaMemsetAsync(s->fp8_scales + SA_GAM, 0, sizeof(float) * (kFp8Scales - SA_GAM), st));
+  nr_render_opts o{};
+  o.mlp_dtype = NR_F32;
+  o.feat_dtype = NR_F32;
+  o.hann_alpha = -1.f;
+  FieldParams P = field_params(s, &o);
+  P.G = s->fp8_G;
+  const size_t smem = sizeof(float) * (P.lay.total + (size_t)(kWidth + kResGammaPad) * kCalThreads);
+  NR_CHECK_CUDA(cudaFuncSetAttribute(calibrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  calibrate_kernel<<<kCalPoints / kCalThreads, kCalThreads, smem, st>>>(P, s->fp8_G + kBones * 12,
+                                                                        s->fp8_scales);
+  finish_scales_kernel<<<1, 32, 0, st>>>(s->fp8_scales, SA_GAM, kFp8Scales - SA_GAM);
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(3);
+  s->fp8_ready = true;
+  return NR_OK;
+}
+
+template <int MODE>
+static nr_status launch_fp8_mode(const FieldParams &P, const Fp8Params &Q, const float4 *in, uint32_t n_fixed,
+                                 const uint32_t *n_dev, float *out, int device, cudaStream_t st) {
+  const Fp8Layout fl = fp8_layout(P.hidden);
+  const TcBias bl = tc_bias_layout(P.hidden);
+  size_t smem = (size_t)((fl.total + 15) & ~15);
+  smem += sizeof(float) * (((bl.total + 3) & ~3) + ((kFp8Scales + 3) & ~3) + kBones * 12);
+  smem += (size_t)kF8Warps * 32 * kF8Row * 2 + sizeof(float) * kF8Warps * 32 * 4;
+  NR_CHECK_CUDA(cudaFuncSetAttribute(field_fp8_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  field_fp8_kernel<MODE><<<num_sms(device), kF8Threads, smem, st>>>(P, Q, in, n_fixed, n_dev, out);
+  NR_CHECK_CUDA(cudaGetLastError());
+  return NR_OK;
+}
+
+nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
+                           float *out, int device, cudaStream_t st) {
+  if (!P.fp8_blob || !P.fp8_scales) {
+    set_error("fp8 tier not prepared");
+    return NR_ESTATE;
+  }
+  Fp8Params Q{P.fp8_blob, P.fp8_scales};
+  return mode == kModeRender ? launch_fp8_mode<kModeRender>(P, Q, in, n_fixed, n_dev, out, device, st)
+                             : launch_fp8_mode<kModeQuery>(P, Q, in, n_fixed, n_dev, out, device, st);
+}
+
+}  // namespace nr

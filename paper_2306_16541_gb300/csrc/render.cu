@@ -188,6 +188,7 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st) {
   if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out,
                                                                           device, st);
+  if (mlp_dtype == NR_FP8E4M3) return launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st);
   if (mlp_dtype != NR_F32) {
     set_error("mlp_dtype %d is not implemented", (int)mlp_dtype);
     return NR_EUNSUPPORTED;
@@ -312,6 +313,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
+  if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const CamParams C = cam_params(cam);
   const uint32_t n_rays = cam->width * cam->height;
@@ -423,6 +425,7 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
+  if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   count_launches(1);
   return launch_field(P, opts->mlp_dtype, kModeQuery, reinterpret_cast<const float4 *>(x_obs), n, nullptr, out,

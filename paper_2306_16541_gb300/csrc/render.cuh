@@ -98,6 +98,8 @@ CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st);
+nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
+                           float *out, int device, cudaStream_t st);
 nr_status launch_field_tc(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st);
 nr_status fold_frame_biases(nr_subject *s, cudaStream_t st);

@@ -273,6 +273,7 @@ extern "C" nr_status nr_server_add_subject(nr_server *srv, nr_subject *s, uint32
   NR_CHECK_CUDA(cudaSetDevice(srv->device));
   nr_status r;
   if ((r = prepare_params(s, nullptr)) != NR_OK) return r;
+  if ((r = prepare_fp8(s, nullptr)) != NR_OK) return r;
   NR_CHECK_CUDA(cudaDeviceSynchronize());
   std::lock_guard<std::mutex> lock(srv->mu);
   NR_REQUIRE(srv->subjects.empty() || srv->subjects[0]->occ_grid == s->occ_grid,
@@ -289,8 +290,9 @@ extern "C" nr_status nr_server_submit(nr_server *srv, const nr_request *req, uin
   NR_REQUIRE(c.width >= 1 && c.height >= 1 && (uint64_t)c.width * c.height <= (1ull << 24),
              "nr_server_submit: image size out of range");
   NR_REQUIRE(c.n_samples >= 1 && c.n_samples <= 1024 && c.fx != 0.f && c.fy != 0.f, "nr_server_submit: bad camera");
-  NR_REQUIRE(req->opts.mlp_dtype == NR_F32 || req->opts.mlp_dtype == NR_BF16 || req->opts.mlp_dtype == NR_F16,
-             "nr_server_submit: mlp_dtype must be NR_F32, NR_BF16 or NR_F16");
+  NR_REQUIRE(req->opts.mlp_dtype == NR_F32 || req->opts.mlp_dtype == NR_BF16 || req->opts.mlp_dtype == NR_F16 ||
+                 req->opts.mlp_dtype == NR_FP8E4M3,
+             "nr_server_submit: unknown mlp_dtype");
   NR_REQUIRE(req->opts.feat_dtype == NR_F32 || req->opts.feat_dtype == NR_F16, "nr_server_submit: bad feat_dtype");
   NR_REQUIRE(req->opts.t_min >= 0.f && req->opts.t_min < 1.f, "nr_server_submit: t_min must be in [0, 1)");
   for (int i = 0; i < kBones * 3; ++i) NR_REQUIRE(isfinite(req->axis_angle[i]), "nr_server_submit: non-finite pose");

@@ -391,6 +391,7 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   count_launches(launched + 1);
   s->params_dirty = false;
   s->bias_dirty = true;
+  s->fp8_ready = false;
   (void)P;
   return NR_OK;
 }
@@ -467,6 +468,8 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   P.tlay = s->tlay;
   P.G = s->d_G;
   P.bias1 = s->d_bias1;
+  P.fp8_blob = s->fp8_blob;
+  P.fp8_scales = s->fp8_scales;
   return P;
 }
 
@@ -486,7 +489,7 @@ static void free_subject(nr_subject *s) {
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
-                  s->loss_acc, s->f_dbias1};
+                  s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)

@@ -206,3 +206,37 @@ def test_tensor_core_query_matches_f32(tiny_structured):
     m = a[:, 3] > 1e-2
     assert np.abs(a[m, 4:7] - b[m, 4:7]).max() < 2e-3    # x_final through the bf16 residual MLP
     assert np.abs(a[m, 8:11] - b[m, 8:11]).max() < 3e-2
+
+
+FP8_PSNR_DB = 50.0   # the reduced-precision bar; e4m3 keeps 3 mantissa bits (elements off by up to 1/16)
+
+
+@pytest.mark.parametrize("which", ["tiny_structured", "frame"])
+def test_fp8_tier_psnr(tiny_structured, frame, which):
+    """FP8 E4M3 MLPs (per-matrix weight scales, calibrated static activation scales) against
+    the oracle; the measured PSNR is printed for the precision table."""
+    if which == "frame":
+        cfg, cam, occ = frame, _small(frame["camera"], 64), True
+    else:
+        cfg, cam, occ = tiny_structured, tiny_structured["camera"], False
+    got = gpu_render(cfg["subject"], cfg["pose"], cam, occ, mlp="fp8", feat="f16" if occ else "f32")
+    ref = oracle_render(cfg["subject"], cfg["pose"], cam, occ).reshape(got.shape)
+    p = psnr(got, ref)
+    print(f"fp8 {which}: PSNR {p:.2f} dB, max abs {np.abs(got - ref).max():.3e}")
+    assert p >= FP8_PSNR_DB
+
+
+def test_fp8_is_batch_independent(tiny_structured):
+    """Static scales: a point's fp8 result is the same whatever else is evaluated with it."""
+    nr = nrmod()
+    cfg = tiny_structured
+    x = torch.from_numpy(np.random.default_rng(8).uniform(-0.9, 0.9, size=(2000, 3)).astype(np.float32)).cuda()
+    S = nr.Subject(cfg["subject"])
+    try:
+        S.set_pose(*cfg["pose"])
+        full = S.query(x, nr.make_opts("fp8"))
+        part = S.query(x[:333].contiguous(), nr.make_opts("fp8"))
+        torch.cuda.synchronize()
+        assert torch.equal(full[:333], part)
+    finally:
+        S.close()
