@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
     p.add_argument("--serve-only", action="store_true", help="run only the serving scenario")
+    p.add_argument("--no-sweep", dest="sweep", action="store_false", help="skip the precision sweep")
+    p.add_argument("--sweep-only", action="store_true", help="run only the precision sweep")
     return p.parse_args()
 
 
@@ -263,6 +265,59 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
                               "mean_service_ms": float(np.mean(service))}}
 
 
+def sweep_bench(nr, device, n_oracle_pixels=384):
+    """Precision sweep: 1920x1080, 192 samples per ray, the tiny workload's field with 2^20
+    entries per level (and a textured variant), no occupancy.  Every MLP tier (f32, bf16, f16,
+    fp8) x hash-feature tier (f32, f16): rays/s (CUDA events), PSNR and max-abs against the FP64
+    oracle on sampled pixels, and PSNR against the f32 GPU image."""
+    import torch
+    from oracle import field as OF
+    from oracle import render as OR
+    from paper_2306_16541_gb300 import synth
+    cfg = synth.config_sweep()
+    cam = cfg["camera"]
+    cam.n_samples = 192
+    out = {}
+    for variant, subj in (("as_configured", cfg["subject"]),
+                          ("textured", synth.subject(1237, log2_t=20, hash_scale=0.5, res_last_std=0.02))):
+        subj = dict(subj)
+        subj["hash_table"] = subj["hash_table"].astype(np.float16).astype(np.float32)   # f16-exact entries
+        rng = np.random.default_rng(11)
+        px = rng.integers(0, cam.width, n_oracle_pixels)
+        py = rng.integers(0, cam.height, n_oracle_pixels)
+        ref = OR.render_pixels(subj, OF.Params(subj), cfg["pose"], cam, px, py, False).numpy()
+        S = nr.Subject(subj, device=device)
+        S.set_pose(*cfg["pose"])
+        img = torch.empty(cam.height, cam.width, 4, device="cuda")
+        base = None
+        rows = []
+        for mlp in ("f32", "bf16", "f16", "fp8"):
+            for feat in ("f32", "f16"):
+                opts = nr.make_opts(mlp, feat, False, 0.0)
+                S.render(cam, opts, img)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                S.render(cam, opts, img)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                got = img.cpu().numpy()
+                if base is None:
+                    base = got.copy()
+                d = got[py, px] - ref
+                mse = float((d ** 2).mean())
+                mse_gpu = float(((got - base) ** 2).mean())
+                rows.append({"mlp": mlp, "feat": feat, "ms": ms, "rays_per_s": cam.width * cam.height / (ms / 1e3),
+                             "psnr_vs_oracle_db": (10 * np.log10(1.0 / mse)) if mse > 0 else float("inf"),
+                             "max_abs_vs_oracle": float(np.abs(d).max()),
+                             "psnr_vs_f32_gpu_db": (10 * np.log10(1.0 / mse_gpu)) if mse_gpu > 0 else float("inf")})
+        S.close()
+        out[variant] = rows
+    return {"workload": "1920x1080, 192 samples, 8x2 levels of 2^20 entries, MLP 32-64-64-4, no occupancy",
+            "oracle_pixels": n_oracle_pixels, "tiers": out}
+
+
 def run_reference(a):
     rank, world, local = dist_setup(a.gpus)
     if rank != 0:
@@ -297,6 +352,9 @@ def run_ours(a):
     from paper_2306_16541_gb300 import nr
     if a.train_only:
         print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays)}))
+        return
+    if a.sweep_only:
+        print(json.dumps({"precision_sweep": sweep_bench(nr, local)}))
         return
     if a.serve_only:
         print(json.dumps({"serving": serve_bench(nr, local, a.mlp, duration=a.serve_seconds)}))
@@ -357,6 +415,7 @@ def run_ours(a):
 
     train = train_bench(nr, local, a.train_steps, n=a.train_rays) if a.train_steps > 0 else None
     serving = serve_bench(nr, local, a.mlp, duration=a.serve_seconds) if a.serve_seconds > 0 else None
+    sweep = sweep_bench(nr, local) if (a.sweep and rank == 0) else None
 
     field_ms = statistics.mean(s["field_ms"] for s in stages)
     live = statistics.mean(s["live_samples"] for s in stages)
@@ -393,6 +452,7 @@ def run_ours(a):
                 "d2h_bytes_per_step": n_rays * 16},
         "train_step": train,
         "serving": serving,
+        "precision_sweep": sweep,
         "gpu_launches": launches,
         "clocks": clk,
     }
