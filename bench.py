@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-pixels", type=int, default=4096)
+    p.add_argument("--cpu-pixels", type=int, default=24576)
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
     p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
