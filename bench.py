@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mma", choices=["tcgen05", "sync"], default="sync",
+                   help="bf16/f16 MLP path: tcgen05.mma with TMEM accumulators, or warp-level mma.sync")
     p.add_argument("--cpu-pixels", type=int, default=24576)
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
@@ -364,7 +366,8 @@ def run_ours(a):
     cam = nr.make_camera(cfg["camera"])
     W, H = cam.width, cam.height
     n_rays = W * H
-    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True)
+    t5 = a.mma == "tcgen05" and a.mlp in ("bf16", "f16")
+    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True, tcgen05=t5)
     S = nr.Subject(cfg["subject"], device=local)
     out = torch.empty(H, W, 4, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -400,7 +403,7 @@ def run_ours(a):
     # end to end through the C ABI with host buffers: pose from host memory,
     # image into pinned host memory (the library copies it back), wall clock
     host_out = torch.empty(H, W, 4, dtype=torch.float32).pin_memory()
-    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4)
+    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4, tcgen05=t5)
     for i in range(2):
         S.set_pose(*poses[i])
         nr.nr_render(S.h, cam, opts_e2e, host_out)
@@ -438,12 +441,15 @@ def run_ours(a):
         "config": {"workload": "frame_512x512_s128_occupancy", "image": [W, H], "samples_per_ray": 128,
                    "occupancy_grid": 128, "hash": "16x2 levels, 2^19 f16 entries, N 16..2048",
                    "mlp": f"32-64-64-64-4 {a.mlp}", "residual_mlp": f"6 PE bands, width 64, {a.mlp}",
+                   "mma_path": ("tcgen05 (TMEM accumulators, M=128 tiles)" if t5 else
+                                ("mma.sync m16n8k16" if a.mlp in ("bf16", "f16") else "CUDA cores")),
                    "weight_volume": "64^3 x 25 f32", "ert_t_min": 1e-4, "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MiB write) between timed steps"},
         "samples_per_s": world * live * a.steps / (total_ms / 1000.0),
         "live_samples_per_frame": live,
         "stage_ms": {k: statistics.mean(st[k] for st in stages) for k in ("march_ms", "field_ms", "composite_ms")},
-        "roofline": {"kernel": "field (fused warp + residual MLP + hash + canonical MLP)", "bound": "hbm",
+        "roofline": {"kernel": ("field_t5_kernel" if t5 else "field kernel") +
+                               " (fused LBS warp + residual MLP + hash + canonical MLP)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "bytes_per_live_sample": bytes_per_sample,

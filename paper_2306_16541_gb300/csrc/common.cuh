@@ -90,6 +90,8 @@ struct FieldParams {
   const float *bias1;                // [64] residual layer-1 bias with the pose folded in
   const uint8_t *fp8_blob;           // e4m3 weight blob (field_fp8.cu)
   const float *fp8_scales;           // its weight and activation scales
+  const uint8_t *t5_bf16, *t5_f16;   // swizzled K-major weight blobs of the tcgen05 path (field_t5.cu)
+  uint32_t *t5_err;                  // set by the tcgen05 path when a bounded wait gives up
 };
 
 struct Frame {                       // a training frame's camera (decoded)
@@ -140,6 +142,9 @@ struct nr_subject {
   void *fp8_jobs = nullptr;
   float *fp8_G = nullptr;
   bool fp8_ready = false;
+  uint8_t *t5_bf16 = nullptr, *t5_f16 = nullptr;
+  uint32_t *t5_err = nullptr;
+  bool t5_ready = false;
   // current pose
   bool pose_set = false;
   float h_G[24 * 12];
@@ -202,6 +207,7 @@ bool subject_ok(const nr_subject *s);
 nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs
 nr_status ensure_bias(nr_subject *s, cudaStream_t st);         // pose-folded bias
 nr_status prepare_fp8(nr_subject *s, cudaStream_t st);         // e4m3 weights + calibrated scales
+nr_status prepare_t5(nr_subject *s, cudaStream_t st);          // swizzled weights of the tcgen05 path
 FieldParams field_params(const nr_subject *s, const nr_render_opts *o);
 nr_status set_error_cuda(cudaError_t e, const char *what);
 }  // namespace nr

@@ -185,7 +185,9 @@ int num_sms(int device) {
 }
 
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
-                       const uint32_t *n_dev, float *out, int device, cudaStream_t st) {
+                       const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path) {
+  if ((mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) && mma_path == 1)
+    return launch_field_t5(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
   if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out,
                                                                           device, st);
   if (mlp_dtype == NR_FP8E4M3) return launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st);
@@ -314,6 +316,8 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
+  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : 0;
+  if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const CamParams C = cam_params(cam);
   const uint32_t n_rays = cam->width * cam->height;
@@ -364,7 +368,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
     NR_CHECK_CUDA(cudaGetLastError());
     NR_CHECK_CUDA(mark(4 * ci + 1));
     if ((r = launch_field(P, opts->mlp_dtype, kModeRender, s->samp, 0, cnt, (float *)s->samp_out, s->device,
-                          st)) != NR_OK)
+                          st, path)) != NR_OK)
       return r;
     NR_CHECK_CUDA(mark(4 * ci + 2));
     composite_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(s->ray_range, s->samp_out, nr_, opts->t_min, cam->bg[0],
@@ -426,8 +430,10 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
+  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : 0;
+  if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   count_launches(1);
   return launch_field(P, opts->mlp_dtype, kModeQuery, reinterpret_cast<const float4 *>(x_obs), n, nullptr, out,
-                      s->device, st);
+                      s->device, st, path);
 }

@@ -392,6 +392,7 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   s->params_dirty = false;
   s->bias_dirty = true;
   s->fp8_ready = false;
+  s->t5_ready = false;
   (void)P;
   return NR_OK;
 }
@@ -470,6 +471,9 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   P.bias1 = s->d_bias1;
   P.fp8_blob = s->fp8_blob;
   P.fp8_scales = s->fp8_scales;
+  P.t5_bf16 = s->t5_bf16;
+  P.t5_f16 = s->t5_f16;
+  P.t5_err = s->t5_err;
   return P;
 }
 
@@ -489,7 +493,8 @@ static void free_subject(nr_subject *s) {
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
-                  s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G};
+                  s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
+                  s->t5_bf16,  s->t5_f16,  s->t5_err};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)

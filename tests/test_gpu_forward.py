@@ -240,3 +240,47 @@ def test_fp8_is_batch_independent(tiny_structured):
         assert torch.equal(full[:333], part)
     finally:
         S.close()
+
+
+def _render_opts(mlp, feat, occ, tcgen05):
+    nr = nrmod()
+    return nr.make_opts(mlp, feat, occ, 0.0, tcgen05=tcgen05)
+
+
+@pytest.mark.parametrize("mlp", ["bf16", "f16"])
+def test_tcgen05_path_psnr_and_agreement(tiny_structured, frame, mlp):
+    """bf16/f16 MLPs on tcgen05.mma with TMEM accumulators: PSNR >= 50 dB against the oracle,
+    and close to the warp-level mma.sync path (same operand rounding, other summation order)."""
+    nr = nrmod()
+    for cfg, cam, occ, feat in ((tiny_structured, tiny_structured["camera"], False, "f32"),
+                                (frame, _small(frame["camera"], 64), True, "f16")):
+        S = nr.Subject(cfg["subject"])
+        try:
+            S.set_pose(*cfg["pose"])
+            a = S.render(cam, _render_opts(mlp, feat, occ, True)).cpu().numpy()
+            b = S.render(cam, _render_opts(mlp, feat, occ, False)).cpu().numpy()
+        finally:
+            S.close()
+        ref = oracle_render(cfg["subject"], cfg["pose"], cam, occ).reshape(a.shape)
+        assert psnr(a, ref) >= 50.0, psnr(a, ref)
+        assert np.abs(a - b).max() <= 2e-2 and psnr(a, b) >= 55.0, (np.abs(a - b).max(), psnr(a, b))
+
+
+def test_tcgen05_query_ragged_tail(tiny_structured):
+    """A point count that leaves a partial 128-sample tile; rows beyond n are never written."""
+    nr = nrmod()
+    cfg = tiny_structured
+    x = torch.from_numpy(np.random.default_rng(9).uniform(-0.9, 0.9, size=(1000, 3)).astype(np.float32)).cuda()
+    S = nr.Subject(cfg["subject"])
+    try:
+        S.set_pose(*cfg["pose"])
+        out = torch.full((1003, nr.NR_QUERY_STRIDE), 7.0, device="cuda")
+        nr.nr_query(S.h, x[:1000].contiguous(), nr.make_opts("bf16", tcgen05=True), out)
+        ref = S.query(x, nr.make_opts("bf16"))
+        torch.cuda.synchronize()
+    finally:
+        S.close()
+    assert (out[1000:] == 7.0).all()
+    a, b = out[:1000].cpu().numpy(), ref.cpu().numpy()
+    assert np.array_equal(a[:, :4], b[:, :4])
+    assert np.abs(a[:, 8:12] - b[:, 8:12]).max() < 2e-2
