@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mma", choices=["tcgen05", "sync"], default="sync",
+    p.add_argument("--mma", choices=["tcgen05", "sync", "sync2"], default="sync",
                    help="bf16/f16 MLP path: tcgen05.mma with TMEM accumulators, or warp-level mma.sync")
     p.add_argument("--cpu-pixels", type=int, default=24576)
     p.add_argument("--train-steps", type=int, default=5)
@@ -367,7 +367,8 @@ def run_ours(a):
     W, H = cam.width, cam.height
     n_rays = W * H
     t5 = a.mma == "tcgen05" and a.mlp in ("bf16", "f16")
-    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True, tcgen05=t5)
+    m2 = a.mma == "sync2"
+    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True, tcgen05=t5, mma2=m2)
     S = nr.Subject(cfg["subject"], device=local)
     out = torch.empty(H, W, 4, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -403,7 +404,7 @@ def run_ours(a):
     # end to end through the C ABI with host buffers: pose from host memory,
     # image into pinned host memory (the library copies it back), wall clock
     host_out = torch.empty(H, W, 4, dtype=torch.float32).pin_memory()
-    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4, tcgen05=t5)
+    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4, tcgen05=t5, mma2=m2)
     for i in range(2):
         S.set_pose(*poses[i])
         nr.nr_render(S.h, cam, opts_e2e, host_out)

@@ -150,7 +150,7 @@ typedef struct {
   uint32_t use_occupancy;  /* skip samples whose posed occupancy cell is empty */
   float t_min;             /* early ray termination once transmittance < t_min; 0 = off */
   float hann_alpha;        /* residual PE window position; < 0 = all bands */
-  uint32_t flags;          /* NR_RENDER_PROFILE | NR_RENDER_TCGEN05, or 0 */
+  uint32_t flags;          /* NR_RENDER_PROFILE | NR_RENDER_TCGEN05 | NR_RENDER_MMA2, or 0 */
 } nr_render_opts;
 
 /* Renders the current pose from `cam` into out_rgba[height][width][4]
@@ -314,6 +314,8 @@ nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out);
 #define NR_RENDER_PROFILE 1u  /* nr_render_opts.flags: time each stage with CUDA events */
 #define NR_RENDER_TCGEN05 2u  /* nr_render_opts.flags: bf16/f16 MLPs on tcgen05.mma with TMEM
                                  accumulators (M = 128 tiles) instead of warp-level mma.sync */
+#define NR_RENDER_MMA2 4u     /* nr_render_opts.flags: warp-level mma.sync over two 16-row tiles per
+                                 weight-fragment read (12 warps/SM instead of 16) */
 
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,

@@ -17,13 +17,17 @@
 
 namespace nr {
 
-constexpr int kTcThreads = 512;
-constexpr int kTcWarps = kTcThreads / 32;
+// Threads per block for MT m-tiles per weight-fragment read (one block per SM).
+template <int MT>
+struct TcCfg {
+  static constexpr int threads = MT == 1 ? 512 : 384;
+  static constexpr int warps = threads / 32;
+};
 constexpr int kGamRow = kResGammaPad + 8;   // 56: gamma tile row stride (elements)
 constexpr int kEncRow = kMlpIn + 8;         // 40: encoding tile row stride (elements)
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, const float4 *__restrict__ in,
+template <typename T, int MODE, int MT>
+__global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldParams P, const float4 *__restrict__ in,
                                                                  uint32_t n_fixed, const uint32_t *__restrict__ n_dev,
                                                                  float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -34,7 +38,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
   // per warp: one [32][kGamRow] tile that holds gamma(x_skel) for the residual MLP and,
   // once that is done, the hash encoding (row stride kEncRow) for the canonical MLP
   T *sGam = reinterpret_cast<T *>(sG + kBones * 12);                     // [warps][32][kGamRow]
-  float *sOut = reinterpret_cast<float *>(sGam + kTcWarps * 32 * kGamRow);  // [warps][32][4]
+  float *sOut = reinterpret_cast<float *>(sGam + TcCfg<MT>::warps * 32 * kGamRow);  // [warps][32][4]
 
   {  // stage weights, biases and the pose's bone transforms
     const int4 *src = reinterpret_cast<const int4 *>(P.tc_blob);
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
   float *o4 = sOut + warp * 32 * 4;
   const uint32_t n = n_dev ? *n_dev : n_fixed;
   const uint32_t n_tiles = (n + 31) / 32;
-  for (uint32_t tile = blockIdx.x * kTcWarps + warp; tile < n_tiles; tile += gridDim.x * kTcWarps) {
+  for (uint32_t tile = blockIdx.x * TcCfg<MT>::warps + warp; tile < n_tiles; tile += gridDim.x * TcCfg<MT>::warps) {
     const uint32_t j = tile * 32 + lane;
     const bool valid = j < n;
     float x0 = 0.f, x1 = 0.f, x2 = 0.f, delta = 0.f;
@@ -115,27 +119,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
       }
       __syncwarp();
 #pragma unroll 1
-      for (int m0 = 0; m0 < 32; m0 += 16) {
-        uint32_t ag[3][4], a[4][4];
-        float acc[8][4];
-        load_a<3>(gam, kGamRow, m0, ag);
+      for (int m0 = 0; m0 < 32; m0 += 16 * MT) {
+        uint32_t ag[MT][3][4], a[MT][4][4];
+        float acc[MT][8][4];
+        load_a<3, MT>(gam, kGamRow, m0, ag);
         init_bias(sBias + bl.r1, acc);
-        mma_block<T, 3, 8>(ag, sW + P.tlay.r1, kTcRow, 0, acc);
-        relu_to_a<T>(acc, a);
+        mma_block<T, 3, 8, MT>(ag, sW + P.tlay.r1, kTcRow, 0, acc);
+        relu_to_a<T, MT>(acc, a);
         init_bias(sBias + bl.r2, acc);
-        mma_block<T, 4, 8>(a, sW + P.tlay.r2, kTcRow, 0, acc);
-        relu_to_a<T>(acc, a);
+        mma_block<T, 4, 8, MT>(a, sW + P.tlay.r2, kTcRow, 0, acc);
+        relu_to_a<T, MT>(acc, a);
         init_bias(sBias + bl.r3, acc);
-        mma_block<T, 4, 8>(a, sW + P.tlay.r3, kTcRow, 0, acc);
-        relu_to_a<T>(acc, a);
+        mma_block<T, 4, 8, MT>(a, sW + P.tlay.r3, kTcRow, 0, acc);
+        relu_to_a<T, MT>(acc, a);
         init_bias(sBias + bl.r4, acc);                               // layer 4 sees [h3, gamma]
-        mma_block<T, 4, 8>(a, sW + P.tlay.r4, kTcRowWide, 0, acc);
-        mma_block<T, 3, 8>(ag, sW + P.tlay.r4, kTcRowWide, kWidth, acc);
-        relu_to_a<T>(acc, a);
-        float acc5[1][4];
+        mma_block<T, 4, 8, MT>(a, sW + P.tlay.r4, kTcRowWide, 0, acc);
+        mma_block<T, 3, 8, MT>(ag, sW + P.tlay.r4, kTcRowWide, kWidth, acc);
+        relu_to_a<T, MT>(acc, a);
+        float acc5[MT][1][4];
         init_bias(sBias + bl.r5, acc5);
-        mma_block<T, 4, 1>(a, sW + P.tlay.r5, kTcRow, 0, acc5);
-        store_out4(acc5, m0, o4);
+        mma_block<T, 4, 1, MT>(a, sW + P.tlay.r5, kTcRow, 0, acc5);
+        store_out4<MT>(acc5, m0, o4);
       }
       __syncwarp();
       f0 += o4[lane * 4 + 0];
@@ -172,22 +176,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
     }
     __syncwarp();
 #pragma unroll 1
-    for (int m0 = 0; m0 < 32; m0 += 16) {
-      uint32_t ae[2][4], a[4][4];
-      float acc[8][4];
-      load_a<2>(enc, kEncRow, m0, ae);
+    for (int m0 = 0; m0 < 32; m0 += 16 * MT) {
+      uint32_t ae[MT][2][4], a[MT][4][4];
+      float acc[MT][8][4];
+      load_a<2, MT>(enc, kEncRow, m0, ae);
       init_bias(sBias + bl.c0, acc);
-      mma_block<T, 2, 8>(ae, sW + P.tlay.c0, kTcRow, 0, acc);
-      relu_to_a<T>(acc, a);
+      mma_block<T, 2, 8, MT>(ae, sW + P.tlay.c0, kTcRow, 0, acc);
+      relu_to_a<T, MT>(acc, a);
       for (int l = 0; l < P.hidden - 1; ++l) {
         init_bias(sBias + bl.c0 + kWidth * (l + 1), acc);
-        mma_block<T, 4, 8>(a, sW + P.tlay.ch[l], kTcRow, 0, acc);
-        relu_to_a<T>(acc, a);
+        mma_block<T, 4, 8, MT>(a, sW + P.tlay.ch[l], kTcRow, 0, acc);
+        relu_to_a<T, MT>(acc, a);
       }
-      float acco[1][4];
+      float acco[MT][1][4];
       init_bias(sBias + bl.cl, acco);
-      mma_block<T, 4, 1>(a, sW + P.tlay.cl, kTcRow, 0, acco);
-      store_out4(acco, m0, o4);
+      mma_block<T, 4, 1, MT>(a, sW + P.tlay.cl, kTcRow, 0, acco);
+      store_out4<MT>(acco, m0, o4);
     }
     __syncwarp();
     if (valid) {
@@ -207,33 +211,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(FieldParams P, 
   }
 }
 
-template <typename T>
+template <typename T, int MT>
 static size_t tc_smem(const FieldParams &P) {
   const TcBias bl = tc_bias_layout(P.hidden);
   size_t b = ((P.tlay.total * sizeof(T) + 15) & ~size_t(15));
   b += sizeof(float) * (((bl.total + 3) & ~3) + kBones * 12);
-  b += sizeof(T) * (size_t)kTcWarps * 32 * kGamRow;
-  b += sizeof(float) * (size_t)kTcWarps * 32 * 4;
+  b += sizeof(T) * (size_t)TcCfg<MT>::warps * 32 * kGamRow;
+  b += sizeof(float) * (size_t)TcCfg<MT>::warps * 32 * 4;
   return b;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int MT>
 static nr_status launch_tc(const FieldParams &P, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev, float *out,
                            int device, cudaStream_t st) {
-  const size_t smem = tc_smem<T>(P);
-  NR_CHECK_CUDA(cudaFuncSetAttribute(field_tc_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  field_tc_kernel<T, MODE><<<num_sms(device), kTcThreads, smem, st>>>(P, in, n_fixed, n_dev, out);
+  const size_t smem = tc_smem<T, MT>(P);
+  NR_CHECK_CUDA(
+      cudaFuncSetAttribute(field_tc_kernel<T, MODE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  field_tc_kernel<T, MODE, MT><<<num_sms(device), TcCfg<MT>::threads, smem, st>>>(P, in, n_fixed, n_dev, out);
   NR_CHECK_CUDA(cudaGetLastError());
   return NR_OK;
 }
 
+template <typename T>
+static nr_status launch_tc_t(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
+                             float *out, int device, cudaStream_t st, int mt) {
+  if (mt == 2)
+    return mode == kModeRender ? launch_tc<T, kModeRender, 2>(P, in, n_fixed, n_dev, out, device, st)
+                               : launch_tc<T, kModeQuery, 2>(P, in, n_fixed, n_dev, out, device, st);
+  return mode == kModeRender ? launch_tc<T, kModeRender, 1>(P, in, n_fixed, n_dev, out, device, st)
+                             : launch_tc<T, kModeQuery, 1>(P, in, n_fixed, n_dev, out, device, st);
+}
+
 nr_status launch_field_tc(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
-                          const uint32_t *n_dev, float *out, int device, cudaStream_t st) {
-  if (mlp_dtype == NR_BF16)
-    return mode == kModeRender ? launch_tc<__nv_bfloat16, kModeRender>(P, in, n_fixed, n_dev, out, device, st)
-                               : launch_tc<__nv_bfloat16, kModeQuery>(P, in, n_fixed, n_dev, out, device, st);
-  return mode == kModeRender ? launch_tc<__half, kModeRender>(P, in, n_fixed, n_dev, out, device, st)
-                             : launch_tc<__half, kModeQuery>(P, in, n_fixed, n_dev, out, device, st);
+                          const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mt) {
+  if (mlp_dtype == NR_BF16) return launch_tc_t<__nv_bfloat16>(P, mode, in, n_fixed, n_dev, out, device, st, mt);
+  return launch_tc_t<__half>(P, mode, in, n_fixed, n_dev, out, device, st, mt);
 }
 
 }  // namespace nr

@@ -55,77 +55,94 @@ __device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
-// The MLP phase runs one 16-row m-tile of the warp's 32 samples at a time, so
-// only one tile's accumulators (32 floats) and A fragments (16 registers) are
-// live; the two tiles reuse the same weight fragments from shared memory.
+// The MLP phase runs MT 16-row m-tiles of the warp's 32 samples per pass: with
+// MT = 1 only one tile's accumulators (32 floats) and A fragments are live; with
+// MT = 2 every weight fragment read from shared memory serves both tiles.
 
-// A fragments of rows m0 .. m0+15 of a row-major [32][lda] tile, K = 16 KT.
-template <int KT, typename T>
-__device__ __forceinline__ void load_a(const T *A, int lda, int m0, uint32_t (&a)[KT][4]) {
+// A fragments of rows m0 + 16 mt .. of a row-major [32][lda] tile, K = 16 KT.
+template <int KT, int MT, typename T>
+__device__ __forceinline__ void load_a(const T *A, int lda, int m0, uint32_t (&a)[MT][KT][4]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int kt = 0; kt < KT; ++kt) ldsm_x4(a[kt], A + (m0 + (lane & 15)) * lda + kt * 16 + (lane >> 4) * 8);
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt)
+      ldsm_x4(a[mt][kt], A + (m0 + 16 * mt + (lane & 15)) * lda + kt * 16 + (lane >> 4) * 8);
 }
 
-// acc[nt] initialised with the bias of columns nt*8 + 2t, +1.
-template <int NT>
-__device__ __forceinline__ void init_bias(const float *bias, float (&acc)[NT][4]) {
+// acc[mt][nt] initialised with the bias of columns nt*8 + 2t, +1.
+template <int NT, int MT>
+__device__ __forceinline__ void init_bias(const float *bias, float (&acc)[MT][NT][4]) {
   const int t = threadIdx.x & 3;
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) {
-    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
-    acc[nt][0] = b0;
-    acc[nt][1] = b1;
-    acc[nt][2] = b0;
-    acc[nt][3] = b1;
+    const float2 b = *reinterpret_cast<const float2 *>(bias + nt * 8 + 2 * t);
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      acc[mt][nt][0] = b.x;
+      acc[mt][nt][1] = b.y;
+      acc[mt][nt][2] = b.x;
+      acc[mt][nt][3] = b.y;
+    }
   }
 }
 
-// acc += A[16 x 16KT] * W^T, W row-major [8NT][ldw] (rows = outputs), columns k0 .. k0 + 16KT.
-template <typename T, int KT, int NT>
-__device__ __forceinline__ void mma_block(const uint32_t (&a)[KT][4], const T *W, int ldw, int k0,
-                                          float (&acc)[NT][4]) {
+// acc += A[16 MT x 16KT] * W^T, W row-major [8NT][ldw] (rows = outputs), columns k0 .. k0 + 16KT.
+template <typename T, int KT, int NT, int MT>
+__device__ __forceinline__ void mma_block(const uint32_t (&a)[MT][KT][4], const T *W, int ldw, int k0,
+                                          float (&acc)[MT][NT][4]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int kt = 0; kt < KT; ++kt) {
     if constexpr (NT == 1) {
       uint32_t b0, b1;
       ldsm_x2(b0, b1, W + (lane & 7) * ldw + k0 + kt * 16 + ((lane >> 3) & 1) * 8);
-      TcOps<T>::mma(acc[0], a[kt], b0, b1);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) TcOps<T>::mma(acc[mt][0], a[mt][kt], b0, b1);
     } else {
 #pragma unroll
       for (int np = 0; np < NT / 2; ++np) {
         uint32_t b[4];
         const int m = lane >> 3, r = lane & 7;
         ldsm_x4(b, W + (np * 16 + (m >> 1) * 8 + r) * ldw + k0 + kt * 16 + (m & 1) * 8);
-        TcOps<T>::mma(acc[2 * np], a[kt], b[0], b[1]);
-        TcOps<T>::mma(acc[2 * np + 1], a[kt], b[2], b[3]);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          TcOps<T>::mma(acc[mt][2 * np], a[mt][kt], b[0], b[1]);
+          TcOps<T>::mma(acc[mt][2 * np + 1], a[mt][kt], b[2], b[3]);
+        }
       }
     }
   }
 }
 
-// ReLU of a 16 x 64 accumulator block, re-packed as the A operand (K = 64) of the next layer.
-template <typename T>
-__device__ __forceinline__ void relu_to_a(const float (&acc)[8][4], uint32_t (&a)[4][4]) {
+// ReLU of a (16 MT) x 64 accumulator block, re-packed as the A operand (K = 64) of the next layer.
+template <typename T, int MT>
+__device__ __forceinline__ void relu_to_a(const float (&acc)[MT][8][4], uint32_t (&a)[MT][4][4]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float *c0 = acc[2 * j], *c1 = acc[2 * j + 1];
-    a[j][0] = TcOps<T>::pack(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
-    a[j][1] = TcOps<T>::pack(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
-    a[j][2] = TcOps<T>::pack(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
-    a[j][3] = TcOps<T>::pack(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
-  }
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float *c0 = acc[mt][2 * j], *c1 = acc[mt][2 * j + 1];
+      a[mt][j][0] = TcOps<T>::pack(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
+      a[mt][j][1] = TcOps<T>::pack(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
+      a[mt][j][2] = TcOps<T>::pack(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
+      a[mt][j][3] = TcOps<T>::pack(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
+    }
 }
 
-// Writes columns 0..3 of a 16 x 8 accumulator block to rows m0.. of out[32][4] (float).
-__device__ __forceinline__ void store_out4(const float (&acc)[1][4], int m0, float *out) {
+// Writes columns 0..3 of a (16 MT) x 8 accumulator block to rows m0.. of out[32][4] (float).
+template <int MT>
+__device__ __forceinline__ void store_out4(const float (&acc)[MT][1][4], int m0, float *out) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   if (t < 2) {
-    out[(m0 + g) * 4 + 2 * t] = acc[0][0];
-    out[(m0 + g) * 4 + 2 * t + 1] = acc[0][1];
-    out[(m0 + g + 8) * 4 + 2 * t] = acc[0][2];
-    out[(m0 + g + 8) * 4 + 2 * t + 1] = acc[0][3];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r0 = m0 + 16 * mt + g;
+      out[r0 * 4 + 2 * t] = acc[mt][0][0];
+      out[r0 * 4 + 2 * t + 1] = acc[mt][0][1];
+      out[(r0 + 8) * 4 + 2 * t] = acc[mt][0][2];
+      out[(r0 + 8) * 4 + 2 * t + 1] = acc[mt][0][3];
+    }
   }
 }
 

@@ -188,8 +188,8 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path) {
   if ((mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) && mma_path == 1)
     return launch_field_t5(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
-  if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out,
-                                                                          device, st);
+  if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16)
+    return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st, mma_path == 2 ? 2 : 1);
   if (mlp_dtype == NR_FP8E4M3) return launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st);
   if (mlp_dtype != NR_F32) {
     set_error("mlp_dtype %d is not implemented", (int)mlp_dtype);
@@ -316,7 +316,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
-  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : 0;
+  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const CamParams C = cam_params(cam);
@@ -430,7 +430,7 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
-  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : 0;
+  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   count_launches(1);

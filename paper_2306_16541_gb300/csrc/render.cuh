@@ -96,7 +96,8 @@ nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t
 
 CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
-// mma_path: 0 = warp-level mma.sync, 1 = tcgen05 (TMEM accumulators) for the bf16/f16 tiers.
+// mma_path for the bf16/f16 tiers: 0 = warp-level mma.sync over one 16-row m-tile per weight-fragment
+// read (16 warps/SM), 1 = tcgen05 (TMEM accumulators), 2 = mma.sync over two m-tiles per read (12 warps/SM).
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path = 0);
 nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
@@ -104,7 +105,7 @@ nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uin
 nr_status launch_field_t5(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st);
 nr_status launch_field_tc(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
-                          const uint32_t *n_dev, float *out, int device, cudaStream_t st);
+                          const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mt);
 nr_status fold_frame_biases(nr_subject *s, cudaStream_t st);
 
 }  // namespace nr
