@@ -169,11 +169,14 @@ struct nr_subject {
   uint32_t *counter = nullptr;       // [4] device counters
   float *out_stage = nullptr;        // [max rays][4] staging for host outputs
   size_t stage_cap = 0;
-  // stage profiling (NR_RENDER_PROFILE): event pairs per stage and chunk
-  static constexpr int kProfEvents = 64;
+  float4 *ray_state = nullptr;       // [max rays] running (C, T) of round-based early termination
+  uint32_t *ray_next = nullptr;      // [max rays] next slot of each ray, top bit = retired
+  // stage profiling (NR_RENDER_PROFILE): a start/end event pair per launch, tagged by stage
+  static constexpr int kProfEvents = 512;
   cudaEvent_t prof_ev[kProfEvents] = {};
-  int prof_used = 0;                 // events recorded by the last profiled render
-  int prof_chunks = 0;
+  int prof_stage[kProfEvents / 2] = {};
+  int prof_used = 0;                 // event pairs recorded by the last profiled render
+  bool prof_overflow = false;
   // training workspace (grow-only)
   size_t tw_samples = 0;             // capacity of t_samp / t_out / t_T
   size_t tw_rays = 0;                // capacity of t_raycnt

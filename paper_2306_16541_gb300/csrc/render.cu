@@ -169,6 +169,134 @@ __global__ void __launch_bounds__(256) composite_kernel(const uint2 *__restrict_
   out[r] = make_float4(fmaf(T, bg0, c0), fmaf(T, bg1, c1), fmaf(T, bg2, c2), 1.f - T);
 }
 
+// ------------------------------------------------------- round-based ERT
+// With early ray termination on, a frame is rendered in rounds so that a ray
+// stops costing field evaluations once it is opaque: each round every active
+// ray appends up to k more live samples (from the slot where the last round
+// stopped), the field runs on that round's queue, and compositing folds them
+// into the ray's running (C, T) and retires the ray when T < t_min or when its
+// slots are exhausted.  The per-ray sequence of compositing operations is the
+// single pass's, so the image is identical.
+constexpr uint32_t kRayDone = 0x80000000u;
+
+__global__ void init_rays_kernel(uint32_t n, float4 *__restrict__ state, uint32_t *__restrict__ next) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) {
+    state[r] = make_float4(0.f, 0.f, 0.f, 1.f);
+    next[r] = 0u;
+  }
+}
+
+// next[r]: the ray's next slot, kRayDone once retired.  The march writes the slot after this
+// round's last sample into next[r] (the composite may then mark the ray done).
+__global__ void __launch_bounds__(256) march_round_kernel(CamParams cam, MarchParams mp, uint32_t k,
+                                                          float4 *__restrict__ samp, uint2 *__restrict__ ray_range,
+                                                          uint32_t *__restrict__ counter, uint32_t *__restrict__ total,
+                                                          uint32_t *__restrict__ next) {
+  const uint32_t r = mp.ray0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = r < mp.ray_end;
+  const uint32_t lane = threadIdx.x & 31;
+  float o[3], d[3], lo = 0.f, hi = 0.f;
+  camera_origin(cam, o);
+  const uint32_t st0 = valid ? next[r - mp.ray0] : kRayDone;
+  bool active = !(st0 & kRayDone);
+  if (active) {
+    const uint32_t u = r % cam.width, v = r / cam.width;
+    active = ray_setup(cam, o, mp.bmin, mp.bmax, u, v, d, lo, hi);
+  }
+  const uint32_t S = cam.n_samples;
+  const float D = __fdiv_rn(__fsub_rn(hi, lo), (float)S);
+  const int G = mp.grid;
+  float h[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) h[q] = __fdiv_rn(__fsub_rn(mp.bmax[q], mp.bmin[q]), (float)G);
+  auto live = [&](uint32_t i, float x[3]) -> bool {
+    const float t = __fadd_rn(lo, __fmul_rn(__fadd_rn((float)i, 0.5f), D));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) x[q] = __fadd_rn(o[q], __fmul_rn(t, d[q]));
+    if (!mp.bits) return true;
+    int c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      int cq = (int)floorf(__fdiv_rn(__fsub_rn(x[q], mp.bmin[q]), h[q]));
+      c[q] = min(max(cq, 0), G - 1);
+    }
+    const uint32_t cell = ((uint32_t)c[2] * G + (uint32_t)c[1]) * G + (uint32_t)c[0];
+    return (__ldg(mp.bits + (cell >> 5)) >> (cell & 31)) & 1u;
+  };
+  const uint32_t i0 = st0 & ~kRayDone;
+  uint32_t count = 0, i_end = S;                      // a ray that misses the box has no slots left
+  if (active) {
+    float x[3];
+    uint32_t i = i0;
+    for (; i < S && count < k; ++i) count += live(i, x) ? 1u : 0u;
+    i_end = i;
+  }
+  uint32_t incl = count;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= (uint32_t)off) incl += y;
+  }
+  const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+  uint32_t base = 0;
+  if (lane == 31 && wtotal) {
+    base = atomicAdd(counter, wtotal);
+    if (total) atomicAdd(total, wtotal);
+  }
+  base = __shfl_sync(0xffffffffu, base, 31);
+  const uint32_t off = base + incl - count;
+  if (valid) {
+    ray_range[r - mp.ray0] = make_uint2(off, count);
+    if (!(st0 & kRayDone)) next[r - mp.ray0] = i_end;
+  }
+  if (count) {
+    uint32_t w = off;
+    for (uint32_t i = i0; w < off + count; ++i) {
+      float x[3];
+      if (live(i, x)) samp[w++] = make_float4(x[0], x[1], x[2], D);
+    }
+  }
+}
+
+// Folds a round's samples into each active ray's (C, T); retires rays below t_min or out of slots.
+__global__ void __launch_bounds__(256) composite_round_kernel(const uint2 *__restrict__ ray_range,
+                                                              const float4 *__restrict__ so, uint32_t n_rays,
+                                                              float t_min, uint32_t S, float4 *__restrict__ state,
+                                                              uint32_t *__restrict__ next) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  const uint32_t nx = next[r];
+  if (nx & kRayDone) return;
+  float4 c = state[r];
+  bool done = false;
+  const uint2 rr = ray_range[r];
+  for (uint32_t i = 0; i < rr.y; ++i) {
+    const float4 v = so[rr.x + i];
+    const float w = c.w * v.w;
+    c.x = fmaf(w, v.x, c.x);
+    c.y = fmaf(w, v.y, c.y);
+    c.z = fmaf(w, v.z, c.z);
+    c.w *= 1.f - v.w;
+    if (c.w < t_min) {
+      done = true;
+      break;
+    }
+  }
+  state[r] = c;
+  if (done || nx >= S) next[r] = nx | kRayDone;
+}
+
+__global__ void add_u32_kernel(uint32_t *__restrict__ acc, const uint32_t *__restrict__ v) { *acc += *v; }
+
+__global__ void finalize_rays_kernel(const float4 *__restrict__ state, uint32_t n_rays, float bg0, float bg1, float bg2,
+                                     float4 *__restrict__ out) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  const float4 c = state[r];
+  out[r] = make_float4(fmaf(c.w, bg0, c.x), fmaf(c.w, bg1, c.y), fmaf(c.w, bg2, c.z), 1.f - c.w);
+}
+
 size_t field_f32_smem(const FieldParams &P) {
   return sizeof(float) * (P.lay.total + kBones * 12 + kWidth + (size_t)kF32ColRows * kF32Threads);
 }
@@ -239,9 +367,15 @@ CamParams cam_params(const nr_camera *c) {
 nr_status grow_workspace(nr_subject *s, size_t rays, size_t samples) {
   if (rays > s->ws_rays) {
     if (s->ray_range) cudaFree(s->ray_range);
+    if (s->ray_state) cudaFree(s->ray_state);
+    if (s->ray_next) cudaFree(s->ray_next);
     s->ray_range = nullptr;
+    s->ray_state = nullptr;
+    s->ray_next = nullptr;
     s->ws_rays = 0;
     NR_CHECK_CUDA(cudaMalloc(&s->ray_range, rays * sizeof(uint2)));
+    NR_CHECK_CUDA(cudaMalloc(&s->ray_state, rays * sizeof(float4)));
+    NR_CHECK_CUDA(cudaMalloc(&s->ray_next, rays * sizeof(uint32_t)));
     s->ws_rays = rays;
   }
   if (samples > s->ws_samples) {
@@ -256,40 +390,99 @@ nr_status grow_workspace(nr_subject *s, size_t rays, size_t samples) {
   return NR_OK;
 }
 
-nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
-                       const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st) {
+// Samples per ray and round when early termination is on (the whole ray otherwise).
+uint32_t round_samples(const nr_camera *cam, const nr_render_opts *opts) {
+  if (opts->t_min <= 0.f) return cam->n_samples;
+  return std::min<uint32_t>(cam->n_samples, std::max<uint32_t>(16u, (cam->n_samples + 3) / 4));
+}
+
+nr_status render_rays(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
+                      const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st, int mma_path,
+                      Prof *prof) {
   const CamParams C = cam_params(cam);
   const uint32_t n_rays = cam->width * cam->height;
-  const uint32_t chunk = (uint32_t)std::min<uint64_t>(
-      std::min<uint64_t>(n_rays, w.cap_rays), std::max<uint64_t>(1, w.cap_samples / cam->n_samples));
-  if (chunk == 0) {
-    set_error("render_frame: workspace too small for one ray");
+  const uint32_t S = cam->n_samples;
+  const uint32_t k = round_samples(cam, opts);
+  const bool rounds = k < S || opts->t_min > 0.f;
+  const uint32_t chunk = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(n_rays, w.cap_rays),
+                                                      std::max<uint64_t>(1, w.cap_samples / k));
+  if (chunk == 0 || (rounds && (!w.state || !w.next))) {
+    set_error("render: workspace too small");
     return NR_EINVAL;
   }
   MarchParams mp{};
-  for (int k = 0; k < 3; ++k) {
-    mp.bmin[k] = s->bmin[k];
-    mp.bmax[k] = s->bmax[k];
+  for (int q = 0; q < 3; ++q) {
+    mp.bmin[q] = s->bmin[q];
+    mp.bmax[q] = s->bmax[q];
   }
   mp.grid = (int)s->occ_grid;
   mp.bits = opts->use_occupancy ? bits : nullptr;
+  auto mark = [&](int stage, bool begin) -> cudaError_t {
+    if (!prof) return cudaSuccess;
+    if (begin) {
+      if (prof->used >= prof->cap) return cudaSuccess;
+      prof->stage[prof->used] = stage;
+      return cudaEventRecord(prof->ev[2 * prof->used], st);
+    }
+    if (prof->used >= prof->cap) {
+      prof->overflow = true;
+      return cudaSuccess;
+    }
+    const cudaError_t e = cudaEventRecord(prof->ev[2 * prof->used + 1], st);
+    prof->used += 1;
+    return e;
+  };
   nr_status r;
+  const uint32_t n_rounds = rounds ? (S + k - 1) / k : 1;
   for (uint32_t r0 = 0; r0 < n_rays; r0 += chunk) {
     const uint32_t nr_ = std::min(chunk, n_rays - r0);
+    const unsigned nb = (nr_ + 255) / 256;
     mp.ray0 = r0;
     mp.ray_end = r0 + nr_;
-    NR_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(uint32_t), st));
-    march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, w.samp, w.ray_range, w.counter);
-    NR_CHECK_CUDA(cudaGetLastError());
-    if ((r = launch_field(P, opts->mlp_dtype, kModeRender, w.samp, 0, w.counter, (float *)w.samp_out, s->device,
-                          st)) != NR_OK)
-      return r;
-    composite_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, cam->bg[0],
-                                                        cam->bg[1], cam->bg[2], dst + r0);
-    NR_CHECK_CUDA(cudaGetLastError());
-    count_launches(3);
+    if (rounds) {
+      init_rays_kernel<<<nb, 256, 0, st>>>(nr_, w.state, w.next);
+      count_launches(1);
+    }
+    for (uint32_t round = 0; round < n_rounds; ++round) {
+      NR_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(uint32_t), st));
+      NR_CHECK_CUDA(mark(0, true));
+      if (rounds)
+        march_round_kernel<<<nb, 256, 0, st>>>(C, mp, k, w.samp, w.ray_range, w.counter, w.total, w.next);
+      else
+        march_kernel<<<nb, 256, 0, st>>>(C, mp, w.samp, w.ray_range, w.counter);
+      NR_CHECK_CUDA(cudaGetLastError());
+      NR_CHECK_CUDA(mark(0, false));
+      if (!rounds && w.total) {
+        add_u32_kernel<<<1, 1, 0, st>>>(w.total, w.counter);
+        count_launches(1);
+      }
+      NR_CHECK_CUDA(mark(1, true));
+      if ((r = launch_field(P, opts->mlp_dtype, kModeRender, w.samp, 0, w.counter, (float *)w.samp_out, s->device, st,
+                            mma_path)) != NR_OK)
+        return r;
+      NR_CHECK_CUDA(mark(1, false));
+      NR_CHECK_CUDA(mark(2, true));
+      if (rounds)
+        composite_round_kernel<<<nb, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, S, w.state, w.next);
+      else
+        composite_kernel<<<nb, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, cam->bg[0], cam->bg[1],
+                                             cam->bg[2], dst + r0);
+      NR_CHECK_CUDA(cudaGetLastError());
+      NR_CHECK_CUDA(mark(2, false));
+      count_launches(3);
+    }
+    if (rounds) {
+      finalize_rays_kernel<<<nb, 256, 0, st>>>(w.state, nr_, cam->bg[0], cam->bg[1], cam->bg[2], dst + r0);
+      NR_CHECK_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
   }
   return NR_OK;
+}
+
+nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
+                       const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st) {
+  return render_rays(s, P, bits, cam, opts, w, dst, st, 0, nullptr);
 }
 
 }  // namespace nr
@@ -319,12 +512,12 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
-  const CamParams C = cam_params(cam);
   const uint32_t n_rays = cam->width * cam->height;
-  // chunk the rays so that the worst-case sample queue stays below 2^26 entries
+  // chunk the rays so that the worst-case sample queue of a round stays below 2^26 entries
   const uint64_t max_samples = 1ull << 26;
-  uint32_t chunk = (uint32_t)std::min<uint64_t>(n_rays, std::max<uint64_t>(256, max_samples / cam->n_samples));
-  if ((r = grow_workspace(s, chunk, (size_t)chunk * cam->n_samples)) != NR_OK) return r;
+  const uint32_t k = round_samples(cam, opts);
+  const uint32_t chunk = (uint32_t)std::min<uint64_t>(n_rays, std::max<uint64_t>(256, max_samples / k));
+  if ((r = grow_workspace(s, chunk, (size_t)chunk * k)) != NR_OK) return r;
   cudaPointerAttributes attr{};
   const bool dev_out = cudaPointerGetAttributes(&attr, out_rgba) == cudaSuccess && attr.type == cudaMemoryTypeDevice;
   cudaGetLastError();
@@ -339,46 +532,34 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
     }
     dst = s->out_stage;
   }
-  MarchParams mp{};
-  for (int k = 0; k < 3; ++k) {
-    mp.bmin[k] = s->bmin[k];
-    mp.bmax[k] = s->bmax[k];
-  }
-  mp.grid = (int)s->occ_grid;
-  mp.bits = opts->use_occupancy ? s->bits : nullptr;
   const bool prof = (opts->flags & NR_RENDER_PROFILE) != 0;
-  const uint32_t n_chunks = (n_rays + chunk - 1) / chunk;
+  Prof pr{};
   if (prof) {
-    NR_REQUIRE(4 * n_chunks <= (uint32_t)nr_subject::kProfEvents && n_chunks <= (uint32_t)kCounters,
-               "nr_render: too many ray chunks to profile");
-    for (uint32_t i = 0; i < 4 * n_chunks; ++i)
+    for (int i = 0; i < nr_subject::kProfEvents; ++i)
       if (!s->prof_ev[i]) NR_CHECK_CUDA(cudaEventCreate(&s->prof_ev[i]));
-    s->prof_used = 0;
-    s->prof_chunks = (int)n_chunks;
+    pr.ev = s->prof_ev;
+    pr.stage = s->prof_stage;
+    pr.cap = nr_subject::kProfEvents / 2;
+    NR_CHECK_CUDA(cudaMemsetAsync(s->counter + 8, 0, 2 * sizeof(uint32_t), st));
   }
-  auto mark = [&](int i) -> cudaError_t { return prof ? cudaEventRecord(s->prof_ev[i], st) : cudaSuccess; };
-  for (uint32_t ci = 0, r0 = 0; r0 < n_rays; ++ci, r0 += chunk) {
-    const uint32_t nr_ = std::min(chunk, n_rays - r0);
-    mp.ray0 = r0;
-    mp.ray_end = r0 + nr_;
-    uint32_t *cnt = s->counter + (ci % kCounters);
-    NR_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));
-    NR_CHECK_CUDA(mark(4 * ci));
-    march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, s->samp, s->ray_range, cnt);
-    NR_CHECK_CUDA(cudaGetLastError());
-    NR_CHECK_CUDA(mark(4 * ci + 1));
-    if ((r = launch_field(P, opts->mlp_dtype, kModeRender, s->samp, 0, cnt, (float *)s->samp_out, s->device,
-                          st, path)) != NR_OK)
-      return r;
-    NR_CHECK_CUDA(mark(4 * ci + 2));
-    composite_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(s->ray_range, s->samp_out, nr_, opts->t_min, cam->bg[0],
-                                                        cam->bg[1], cam->bg[2],
-                                                        reinterpret_cast<float4 *>(dst) + r0);
-    NR_CHECK_CUDA(cudaGetLastError());
-    NR_CHECK_CUDA(mark(4 * ci + 3));
-    count_launches(3);
+  FrameWork w{};
+  w.samp = s->samp;
+  w.samp_out = s->samp_out;
+  w.ray_range = s->ray_range;
+  w.counter = s->counter;
+  w.total = prof ? s->counter + 8 : nullptr;
+  w.state = s->ray_state;
+  w.next = s->ray_next;
+  w.cap_samples = s->ws_samples;
+  w.cap_rays = s->ws_rays;
+  s->prof_used = 0;
+  if ((r = render_rays(s, P, s->bits, cam, opts, w, reinterpret_cast<float4 *>(dst), st, path, prof ? &pr : nullptr)) !=
+      NR_OK)
+    return r;
+  if (prof) {
+    s->prof_used = pr.used;
+    s->prof_overflow = pr.overflow;
   }
-  if (prof) s->prof_used = 4 * (int)n_chunks;
   if (!dev_out) {
     NR_CHECK_CUDA(cudaMemcpyAsync(out_rgba, dst, (size_t)n_rays * 16, cudaMemcpyDeviceToHost, st));
     NR_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -393,24 +574,26 @@ extern "C" nr_status nr_stage_times(nr_subject *s, float *ms) {
     return NR_ESTATE;
   }
   NR_CHECK_CUDA(cudaSetDevice(s->device));
-  NR_CHECK_CUDA(cudaEventSynchronize(s->prof_ev[s->prof_used - 1]));
+  NR_CHECK_CUDA(cudaEventSynchronize(s->prof_ev[2 * s->prof_used - 1]));
   float acc[3] = {0.f, 0.f, 0.f};
-  for (int c = 0; c < s->prof_chunks; ++c)
-    for (int k = 0; k < 3; ++k) {
-      float t = 0.f;
-      NR_CHECK_CUDA(cudaEventElapsedTime(&t, s->prof_ev[4 * c + k], s->prof_ev[4 * c + k + 1]));
-      acc[k] += t;
-    }
-  uint32_t live[kCounters];
-  const int nc = std::min(s->prof_chunks, kCounters);
-  NR_CHECK_CUDA(cudaMemcpy(live, s->counter, sizeof(uint32_t) * nc, cudaMemcpyDeviceToHost));
-  double total = 0;
-  for (int c = 0; c < nc; ++c) total += live[c];
+  int field_launches = 0;
+  for (int i = 0; i < s->prof_used; ++i) {
+    float t = 0.f;
+    NR_CHECK_CUDA(cudaEventElapsedTime(&t, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]));
+    acc[s->prof_stage[i]] += t;
+    field_launches += s->prof_stage[i] == 1;
+  }
+  uint32_t live = 0;
+  NR_CHECK_CUDA(cudaMemcpy(&live, s->counter + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   ms[0] = acc[0];
   ms[1] = acc[1];
   ms[2] = acc[2];
-  ms[3] = (float)s->prof_chunks;
-  ms[4] = (float)total;
+  ms[3] = (float)field_launches;
+  ms[4] = (float)live;
+  if (s->prof_overflow) {
+    set_error("nr_stage_times: more launches than profiling events; times are partial");
+    return NR_EBUSY;
+  }
   return NR_OK;
 }
 

@@ -86,9 +86,25 @@ __global__ void composite_kernel(const uint2 *__restrict__ ray_range, const floa
 struct FrameWork {
   float4 *samp, *samp_out;        // [cap_samples]
   uint2 *ray_range;               // [cap_rays]
-  uint32_t *counter;              // [1]
+  uint32_t *counter;              // [1] live samples of the current round
+  uint32_t *total;                // [2] live samples over the frame (profiling), or NULL
+  float4 *state;                  // [cap_rays] running (C, T) for round-based early termination
+  uint32_t *next;                 // [cap_rays] next slot / retired flag
   size_t cap_samples, cap_rays;
 };
+
+// Start/end CUDA-event pairs recorded around each launch of a profiled render.
+struct Prof {
+  cudaEvent_t *ev;                // 2 * cap events
+  int *stage;                     // [cap] 0 march, 1 field, 2 composite
+  int cap, used;
+  bool overflow;
+};
+
+uint32_t round_samples(const nr_camera *cam, const nr_render_opts *opts);
+nr_status render_rays(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
+                      const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st, int mma_path,
+                      Prof *prof);
 // Renders `cam` for the pose whose transforms / folded bias are in P (P.G, P.bias1) and whose posed
 // occupancy bitfield is `bits` into the device buffer dst[height * width], in ray chunks that fit w.
 nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,

@@ -91,15 +91,15 @@ struct DoneCtx {
 static bool server_ok(const nr_server *s) { return s && s->magic == 0x4e525356u; }
 
 static size_t slot_bytes(int grid) {
-  return kSlotSamples * 2 * sizeof(float4) + kSlotRays * sizeof(uint2) + 256 + (size_t)grid * grid * grid / 8 +
-         (kBones * 12 + kBones * 3 + kWidth) * sizeof(float);
+  return kSlotSamples * 2 * sizeof(float4) + kSlotRays * (sizeof(uint2) + sizeof(float4) + sizeof(uint32_t)) + 256 +
+         (size_t)grid * grid * grid / 8 + (kBones * 12 + kBones * 3 + kWidth) * sizeof(float);
 }
 
 static void free_slot(Slot *sl) {
   if (!sl) return;
   if (sl->stream) cudaStreamSynchronize(sl->stream);
-  void *bufs[] = {sl->d_G, sl->d_omega, sl->d_bias1, sl->bits, sl->w.samp, sl->w.samp_out, sl->w.ray_range,
-                  sl->w.counter};
+  void *bufs[] = {sl->d_G,       sl->d_omega,   sl->d_bias1,      sl->bits,   sl->w.samp,
+                  sl->w.samp_out, sl->w.ray_range, sl->w.counter, sl->w.state, sl->w.next};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (sl->h_pose) cudaFreeHost(sl->h_pose);
@@ -127,6 +127,8 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
   SLOT_ALLOC(sl->w.samp_out, kSlotSamples * sizeof(float4));
   SLOT_ALLOC(sl->w.ray_range, kSlotRays * sizeof(uint2));
   SLOT_ALLOC(sl->w.counter, 256);
+  SLOT_ALLOC(sl->w.state, kSlotRays * sizeof(float4));
+  SLOT_ALLOC(sl->w.next, kSlotRays * sizeof(uint32_t));
 #undef SLOT_ALLOC
   if ((e = cudaMallocHost((void **)&sl->h_pose, (kBones * 12 + kBones * 3) * sizeof(float))) != cudaSuccess)
     return fail(e, "pinned pose buffer");

@@ -494,7 +494,7 @@ static void free_subject(nr_subject *s) {
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
-                  s->t5_bf16,  s->t5_f16,  s->t5_err};
+                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)

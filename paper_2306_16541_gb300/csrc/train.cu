@@ -24,7 +24,6 @@
 namespace nr {
 
 constexpr int kBwdThreads = 128;
-constexpr int kBwdWarps = kBwdThreads / 32;
 
 // Rows of a thread's scratch column (sized for the subject's hidden depth H).
 struct Rows {

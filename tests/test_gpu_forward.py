@@ -284,3 +284,58 @@ def test_tcgen05_query_ragged_tail(tiny_structured):
     a, b = out[:1000].cpu().numpy(), ref.cpu().numpy()
     assert np.array_equal(a[:, :4], b[:, :4])
     assert np.abs(a[:, 8:12] - b[:, 8:12]).max() < 2e-2
+
+
+def test_bench_configuration_sampled_against_oracle(frame):
+    """The frame exactly as bench.py times it (512x512, 128 samples, occupancy, f16 table,
+    bf16 MLPs on the default path, ERT at 1e-4): 2000 sampled pixels against the oracle.
+    ERT changes a pixel by at most T_min, inside the PSNR budget."""
+    nr = nrmod()
+    cam = frame["camera"]
+    S = nr.Subject(frame["subject"])
+    try:
+        S.set_pose(*frame["pose"])
+        img = S.render(cam, nr.make_opts("bf16", "f16", True, 1e-4)).cpu().numpy()
+    finally:
+        S.close()
+    rng = np.random.default_rng(5)
+    px = rng.integers(0, cam.width, 2000)
+    py = rng.integers(0, cam.height, 2000)
+    ref = oracle_render(frame["subject"], frame["pose"], cam, True, px, py)
+    got = img[py, px]
+    assert psnr(got, ref) >= 50.0
+    assert np.abs(got - ref).max() <= 1e-2
+
+
+def test_round_based_termination_saves_work_and_matches_single_pass(tiny_structured):
+    """Early termination in rounds: an opaque performer evaluates fewer samples than without
+    termination, and the image equals the single-pass compositor that stops at the same T_min
+    (nr_render_static composites every queued sample in one pass)."""
+    import ctypes as C
+    nr = nrmod()
+    cfg = tiny_structured
+    s = synth.subject(78, hash_scale=0.5)
+    s["mlp_layers"][-1][1][3] = 40.0                      # opaque: rays terminate after a few samples
+    s["mlp_params"] = synth.pack_layers(s["mlp_layers"])
+    s["wvol"] = np.full_like(s["wvol"], 1.0 / 25.0)       # S = 24/25 everywhere in the box
+    c = synth.camera(64, 64, 80.0, (0.0, 0.0, 2.5), 64, 1.5, 3.5)
+    c.R, c.t = cfg["camera"].R, cfg["camera"].t
+    cam = nr.make_camera(c)                               # 64 samples: four rounds of 16
+    S = nr.Subject(s)
+    try:
+        S.set_pose(*cfg["pose"])
+        on = nr.make_opts("f32", "f32", False, 1e-4, profile=True)
+        off = nr.make_opts("f32", "f32", False, 0.0, profile=True)
+        a = S.render(cam, on).clone()
+        live_on = S.stage_times()["live_samples"]
+        S.render(cam, off)
+        live_off = S.stage_times()["live_samples"]
+        b = torch.empty_like(a)
+        rc = nr.lib.nr_render_static(S.h, C.byref(cam), C.byref(nr.make_opts("f32", "f32", False, 1e-4)),
+                                     C.c_void_p(b.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == nr.NR_OK
+        torch.cuda.synchronize()
+    finally:
+        S.close()
+    assert live_on < 0.4 * live_off, (live_on, live_off)
+    assert torch.equal(a, b)
