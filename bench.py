@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
     p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
+    p.add_argument("--train-layout", choices=["uniform", "patch"], default="uniform",
+                   help="uniform random pixels, or 6 patches of 20x20 per image with MSE weight 0.2")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
     p.add_argument("--serve-only", action="store_true", help="run only the serving scenario")
     p.add_argument("--no-sweep", dest="sweep", action="store_false", help="skip the precision sweep")
@@ -148,11 +150,13 @@ def cpu_baseline(cfg, poses, n_pixels, seed=0):
                        f"FP64 torch CPU, no early termination), {dt:.1f} s")
 
 
-def train_bench(nr, device, steps, warmup=2, n=1 << 18):
+def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform"):
     """Training-step time on the training workload: 16 frames of 512x512 with seeded
     poses, targets rendered from a seeded ground-truth field of the tiny workload's
     shape, 2^18 random pixel rays x 128 stratified samples, forward + backward +
-    Adam (lr 1e-2, beta (0.9, 0.99)).  CUDA events on the training stream."""
+    Adam (lr 1e-2, beta (0.9, 0.99)).  CUDA events on the training stream.
+    layout "patch" draws the rays as 6 patches of 20x20 pixels per image (110 images,
+    264,000 rays) and weights the MSE by 0.2 (Sec. 5.2)."""
     import torch
     from paper_2306_16541_gb300 import synth
     gt = synth.subject(700, hash_scale=0.5, res_last_std=0.02)
@@ -171,25 +175,37 @@ def train_bench(nr, device, steps, warmup=2, n=1 << 18):
     Sub.set_frames(frames["axis_angle"], frames["root_t"], frames["cameras"])
     gen = torch.Generator(device="cuda").manual_seed(702)
     batches = []
-    for _ in range(steps + warmup):
-        f = torch.randint(0, 16, (n,), device="cuda", generator=gen, dtype=torch.int32)
-        px = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
-        py = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
+    weight = 0.0
+    if layout == "patch":
+        weight = nr.PAPER_MSE_WEIGHT
+        n_img = (n + 2399) // 2400
+        n = n_img * 2400
+    for k in range(steps + warmup):
+        if layout == "patch":
+            pb = synth.patch_batch(710 + k, 16, n_img)
+            f, px, py = (torch.from_numpy(pb[c].astype(np.int32)).cuda() for c in ("frame", "px", "py"))
+        else:
+            f = torch.randint(0, 16, (n,), device="cuda", generator=gen, dtype=torch.int32)
+            px = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
+            py = torch.randint(0, 512, (n,), device="cuda", generator=gen, dtype=torch.int32)
         batches.append((f, px, py, targets[f.long(), py.long(), px.long()].contiguous()))
     losses = []
     for k in range(warmup):
-        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE))
+        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE,
+                                     loss_weight=weight))
     torch.cuda.synchronize()
     ms = []
     for k in range(warmup, warmup + steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE))
+        losses.append(Sub.train_step(*batches[k], 128, 5000 + k, lr=1e-2, lr_scale=nr.PAPER_LR_SCALE,
+                                     loss_weight=weight))
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     Sub.close()
-    return {"workload": f"16 frames 512x512, {n} rays x 128 samples, fp32 forward+backward+Adam",
+    shape = "6 patches of 20x20 per image, MSE weight 0.2" if layout == "patch" else "uniform pixels"
+    return {"workload": f"16 frames 512x512, {n} rays ({shape}) x 128 samples, fp32 forward+backward+Adam",
             "lr": "1e-2 (hash, canonical MLP), 1e-3 (weight volume, residual MLP)",
             "ms": statistics.mean(ms), "ms_min": min(ms), "steps": steps, "warmup": warmup,
             "rays_per_s": n / (statistics.mean(ms) / 1000.0),
@@ -353,7 +369,7 @@ def run_ours(a):
     barrier(world)
     from paper_2306_16541_gb300 import nr
     if a.train_only:
-        print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays)}))
+        print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays, layout=a.train_layout)}))
         return
     if a.sweep_only:
         print(json.dumps({"precision_sweep": sweep_bench(nr, local)}))
@@ -417,7 +433,7 @@ def run_ours(a):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = world * n_rays * a.steps / e2e_s
 
-    train = train_bench(nr, local, a.train_steps, n=a.train_rays) if a.train_steps > 0 else None
+    train = train_bench(nr, local, a.train_steps, n=a.train_rays, layout=a.train_layout) if a.train_steps > 0 else None
     serving = serve_bench(nr, local, a.mlp, duration=a.serve_seconds) if a.serve_seconds > 0 else None
     sweep = sweep_bench(nr, local) if (a.sweep and rank == 0) else None
 

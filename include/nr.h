@@ -76,7 +76,9 @@ typedef struct nr_subject nr_subject;   /* opaque, library-owned */
  *   W4[64][64 + g], b4, W5[3][64], b5.
  * Occupancy: ellipsoids[n_bones][15] (centre[3], rotation rows[9] mapping
  *   canonical to the ellipsoid's local frame, radii[3]) in canonical space, or
- *   NULL for no occupancy support; occ_grid cells per axis (a multiple of 8).
+ *   NULL; occ_grid cells per axis of the occupancy grids (32, 64, 128 or 256;
+ *   0 = 128), used by the ellipsoids or by a canonical density grid
+ *   (nr_refresh_occupancy).
  */
 typedef struct {
   uint32_t abi_version;          /* NR_ABI_VERSION */
@@ -226,9 +228,11 @@ typedef struct {
   float lr_scale[4];             /* per-group multiplier of lr: weight volume, hash table,
                                     canonical MLP, residual MLP; 0 means 1.  Sec. 5.2 trains
                                     the NeRF network with a 10x larger rate than the others. */
+  float loss_weight;             /* lambda_mse: L = lambda_mse * MSE (Sec. 5.2 uses 0.2 beside
+                                    LPIPS); 0 means 1 */
 } nr_train_batch;
 
-/* Forward, loss L = mean over rays and channels of (C^ - C_gt)^2, the
+/* Forward, loss L = loss_weight * mean over rays and channels of (C^ - C_gt)^2, the
  * hand-written backward into the gradient buffers (overwritten, not
  * accumulated), then one Adam step (bias-corrected, every entry updated)
  * on the selected groups.  loss_out (host, may be NULL) receives L after
@@ -308,8 +312,36 @@ nr_status nr_server_destroy(nr_server *srv);
 /* Copies the current pose's float32 transforms G[n_bones][12] (host). */
 nr_status nr_pose_transforms(nr_subject *s, float *G_out);
 /* Copies the current posed occupancy bitfield (occ_grid^3 / 32 uint32, host);
- * cell (x, y, z) is bit (z * g + y) * g + x. */
+ * cell (x, y, z) is bit (z * g + y) * g + x.  NR_ESTATE without a pose or an
+ * occupancy source. */
 nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out);
+
+/* Occupancy from the field's own density: empty-space skipping (Sec. 2.3) for
+ * subjects with no ellipsoids, or after training has moved the performer's
+ * surface.  Both calls make a canonical grid the subject's occupancy source
+ * (ellipsoids, if any, are no longer used); the grid has occ_grid^3 cells over
+ * the box, in the layout of nr_occupancy.
+ *
+ * nr_refresh_occupancy evaluates, in float32 on CUDA cores with the float32
+ * hash table, the canonical density sigma = softplus(o_3) of MLP_nerf at the
+ * centre bmin + (j + 0.5) h of every canonical cell (h = (bmax - bmin) /
+ * occ_grid), marks the cells with sigma > sigma_threshold and dilates the set
+ * by `dilate` cells (0..3, Chebyshev distance, clipped at the grid's faces).
+ * Call it again whenever the parameters have moved far enough (a periodic
+ * refresh during training).  nr_set_canonical_occupancy installs a given
+ * canonical bitfield (host, occ_grid^3 / 32 words) instead.
+ *
+ * Posing: observed cell c is set iff at its centre y the bone-weight sum
+ * S(y) >= s_min and the canonical cell clamp(floor((x_final - bmin) / h), 0,
+ * occ_grid - 1) is set, x_final(y) being the canonical point of Eq. lbs and
+ * MLP_res with every PE band on (float32).  The posed grid is rebuilt lazily by the
+ * next render, query of nr_occupancy or served request after nr_set_pose, a
+ * training step, nr_params_changed or either call here.
+ * Errors: NR_EINVAL for a bad threshold, dilate or s_min; NR_ENOMEM. */
+nr_status nr_refresh_occupancy(nr_subject *s, float sigma_threshold, uint32_t dilate, float s_min, void *stream);
+nr_status nr_set_canonical_occupancy(nr_subject *s, const uint32_t *bits, float s_min, void *stream);
+/* Copies the canonical bitfield of a canonical-grid source (host); NR_ESTATE otherwise. */
+nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
 
 #define NR_RENDER_PROFILE 1u  /* nr_render_opts.flags: time each stage with CUDA events */
 #define NR_RENDER_TCGEN05 2u  /* nr_render_opts.flags: bf16/f16 MLPs on tcgen05.mma with TMEM

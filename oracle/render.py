@@ -93,11 +93,13 @@ def pose_inputs(subj: dict, axis_angle, root_t):
 
 
 def render_pixels(subj: dict, P: Params, pose, cam, px, py, use_occupancy: bool,
-                  grid: int = 128, chunk: int = 1024, alpha=None, return_counts: bool = False):
+                  grid: int = 128, chunk: int = 1024, alpha=None, return_counts: bool = False,
+                  bits=None):
     """RGBA [N][4] (float64) of pixels (px, py) for one pose and camera.
 
     The box-hit and occupancy decisions come from `decide32` (float32, the
-    kernel's precision); everything else is FP64.
+    kernel's precision); everything else is FP64.  `bits` (uint32 words of a
+    grid^3 posed bitfield) replaces the ellipsoid bitfield when given.
     """
     axis_angle, root_t = pose
     G_R, G_t, omega = pose_inputs(subj, axis_angle, root_t)
@@ -107,8 +109,9 @@ def render_pixels(subj: dict, P: Params, pose, cam, px, py, use_occupancy: bool,
     lo32, hi32, hit32 = decide32.clip32(o32, d32, cam.t_near, cam.t_far, subj["box_min"], subj["box_max"])
     S = cam.n_samples
     if use_occupancy:
-        G32 = fk.bone_transforms_f32(subj["parents"], subj["rest_joints"], axis_angle, root_t)
-        bits = decide32.posed_bitfield32(G32, subj["ellipsoids"], subj["box_min"], subj["box_max"], grid)
+        if bits is None:
+            G32 = fk.bone_transforms_f32(subj["parents"], subj["rest_joints"], axis_angle, root_t)
+            bits = decide32.posed_bitfield32(G32, subj["ellipsoids"], subj["box_min"], subj["box_max"], grid)
         x32 = decide32.sample_points32(o32, d32, lo32, hi32, S)
         live = decide32.bit_test(bits, decide32.cell_of32(x32, subj["box_min"], subj["box_max"], grid))
         live &= hit32[:, None]
@@ -147,8 +150,9 @@ def render_image(subj: dict, pose, cam, use_occupancy: bool, **kw) -> torch.Tens
 
 
 def train_loss(subj: dict, P: Params, frames: dict, batch: dict, target_rgb, step_seed: int,
-               n_samples: int, bg, alpha=None, ray_offset: int = 0):
-    """Mean squared error over rays and channels of one training batch (no occupancy, no ERT).
+               n_samples: int, bg, alpha=None, ray_offset: int = 0, loss_weight: float = 1.0):
+    """loss_weight x mean squared error over rays and channels of one training batch (no
+    occupancy, no ERT); Sec. 5.2 weights the MSE term by lambda_mse = 0.2.
 
     frames: axis_angle [F][24][3], root_t [F][3], cameras [F]; batch: frame, px, py [N].
     """
@@ -182,4 +186,4 @@ def train_loss(subj: dict, P: Params, frames: dict, batch: dict, target_rgb, ste
         pred_list.append((torch.from_numpy(rows), rgba[:, :3]))
     for rows, rgb in pred_list:
         pred = pred.index_put((rows,), rgb)
-    return ((pred - tgt) ** 2).mean(), pred
+    return loss_weight * ((pred - tgt) ** 2).mean(), pred

@@ -92,6 +92,11 @@ struct FieldParams {
   const float *fp8_scales;           // its weight and activation scales
   const uint8_t *t5_bf16, *t5_f16;   // swizzled K-major weight blobs of the tcgen05 path (field_t5.cu)
   uint32_t *t5_err;                  // set by the tcgen05 path when a bounded wait gives up
+  // occupancy from the field's density (kModeDensity / kModePose of the FP32 kernel)
+  int occ_grid;                      // cells per axis
+  float occ_tau;                     // density threshold
+  float occ_smin;                    // least bone-weight sum S of a posed cell
+  const uint32_t *canon_bits;        // canonical bitfield read by kModePose
 };
 
 struct Frame {                       // a training frame's camera (decoded)
@@ -116,6 +121,7 @@ struct nr_subject {
   uint32_t res_enabled = 0, res_freqs = 0;
   uint32_t occ_grid = 128;
   bool has_ellipsoids = false;
+  uint32_t occ_source = 0;           // kOccNone, kOccEllipsoids or kOccGrid
   std::vector<int> parents;
   std::vector<double> rest;          // [K][3]
   // float32 master parameters and their gradients
@@ -154,7 +160,11 @@ struct nr_subject {
   float *d_bias1 = nullptr;          // [64]
   bool bias_dirty = true;
   float *ellip = nullptr;            // [24][15]
-  uint32_t *bits = nullptr;          // occ_grid^3 / 32
+  uint32_t *bits = nullptr;          // occ_grid^3 / 32, posed
+  uint32_t *canon_bits = nullptr;    // occ_grid^3 / 32, canonical (kOccGrid)
+  uint32_t *occ_raw = nullptr;       // occ_grid^3 / 32, undilated density test
+  float occ_smin = 0.f;              // least bone-weight sum of a posed cell (kOccGrid)
+  bool occ_dirty = false;            // posed grid stale (kOccGrid)
   // training frames
   uint32_t n_frames = 0, frames_cap = 0;
   float *f_G = nullptr;              // [F][24][12]
@@ -204,7 +214,11 @@ MasterOffsets master_offsets(const nr_subject *s);
 int res_gamma_dims(const nr_subject *s);
 void count_launches(uint64_t n);                              // kernels launched by the library
 void forward_kinematics(const nr_subject *s, const float *aa, const float *root_t, float *G);   // host, fp64 -> fp32
-nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, uint32_t *bits, cudaStream_t st);
+constexpr uint32_t kOccNone = 0, kOccEllipsoids = 1, kOccGrid = 2;   // nr_subject::occ_source
+nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const float *bias_dev, uint32_t *bits,
+                                cudaStream_t st);
+nr_status ensure_occupancy(nr_subject *s, cudaStream_t st);    // posed grid of the current pose (kOccGrid)
+nr_status launch_occupancy_field(const FieldParams &P, int mode, uint32_t *bits, int device, cudaStream_t st);
 nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *bias_dev, int n_poses, cudaStream_t st);
 bool subject_ok(const nr_subject *s);
 nr_status prepare_params(nr_subject *s, cudaStream_t st);      // derived blobs

@@ -83,6 +83,18 @@ __global__ void __launch_bounds__(256) march_kernel(CamParams cam, MarchParams m
 // transposed), read as broadcast float4.  Writes (r, g, b, alpha) per sample
 // with alpha = (1 - exp(-sigma delta)) * min(S, 1) (Sec. 4.4 likelihood
 // augmentation), zero when the canonical point leaves the box.
+//
+// Two more modes build occupancy bitfields from the field itself (empty-space
+// skipping for subjects without ellipsoids, Sec. 2.3), one thread per cell of
+// an occ_grid^3 grid over the box, cell centre y_k = bmin_k + ((j_k + 0.5) h_k):
+//   kModeDensity: y is canonical; bit = softplus(o_3(enc(y))) > occ_tau.
+//   kModePose:    y is observed; bit = S(y) >= occ_smin and canon_bits holds the
+//                 canonical cell clamp(floor((x_final(y) - bmin) / h), 0, G - 1)
+//                 (x_final: Eq. lbs then MLP_res, as for a sample).  The clamp
+//                 keeps a cell whose centre maps just outside the box while
+//                 other points of the cell map inside.
+// Cells are word-aligned per warp (occ_grid^3 is a multiple of 32 and so are
+// the block and the grid stride), so a warp ballot writes whole words.
 constexpr int kF32Threads = 192;
 constexpr int kF32ColRows = kWidth + kResGammaPad;   // per-thread activation column: h (64) then gamma (48)
 
@@ -103,7 +115,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
   const int stride = blockDim.x;
   float *hcol = sCol + threadIdx.x;
   float *gcol = hcol + kWidth * stride;
-  const uint32_t n = n_dev ? *n_dev : n_fixed;
+  constexpr bool kCells = MODE == kModeDensity || MODE == kModePose;
+  float h[3] = {0.f, 0.f, 0.f};
+  if (kCells) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = __fdiv_rn(__fsub_rn(P.bmax[k], P.bmin[k]), (float)P.occ_grid);
+  }
+  const uint32_t n = kCells ? (uint32_t)P.occ_grid * P.occ_grid * P.occ_grid : (n_dev ? *n_dev : n_fixed);
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     float x0, x1, x2, delta = 0.f;
     if (MODE == kModeRender) {
@@ -112,15 +130,52 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
       x1 = s.y;
       x2 = s.z;
       delta = s.w;
-    } else {
+    } else if (MODE == kModeQuery) {
       const float *q = reinterpret_cast<const float *>(in) + 3 * (size_t)j;
       x0 = q[0];
       x1 = q[1];
       x2 = q[2];
+    } else {
+      const uint32_t g = (uint32_t)P.occ_grid;
+      x0 = __fadd_rn(P.bmin[0], __fmul_rn(__fadd_rn((float)(j % g), 0.5f), h[0]));
+      x1 = __fadd_rn(P.bmin[1], __fmul_rn(__fadd_rn((float)((j / g) % g), 0.5f), h[1]));
+      x2 = __fadd_rn(P.bmin[2], __fmul_rn(__fadd_rn((float)(j / (g * g)), 0.5f), h[2]));
+    }
+    if (MODE == kModeDensity) {
+      hash_encode(P, x0, x1, x2, hcol, stride);
+      float o[4];
+      canonical_f32(P, sW, hcol, stride, o);
+      const unsigned word = __ballot_sync(0xffffffffu, softplusf_(o[3]) > P.occ_tau);
+      if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(out)[j >> 5] = word;
+      continue;
     }
     float s0, s1, s2, S;
     lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
     float f0 = s0, f1 = s1, f2 = s2;
+    if (MODE == kModePose) {
+      bool occ = false;
+      if (S >= P.occ_smin) {
+        if (P.res_enabled) {
+          pos_enc(P, s0, s1, s2, gcol, stride);
+          float r0, r1, r2;
+          residual_f32(P, sW, sB1, gcol, hcol, stride, r0, r1, r2);
+          f0 += r0;
+          f1 += r1;
+          f2 += r2;
+        }
+        // clamped to the grid as floats before the conversion (fmaxf maps NaN to 0)
+        const float top = (float)(P.occ_grid - 1);
+        const float c0 = fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(f0, P.bmin[0]), h[0])), 0.f), top);
+        const float c1 = fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(f1, P.bmin[1]), h[1])), 0.f), top);
+        const float c2 = fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(f2, P.bmin[2]), h[2])), 0.f), top);
+        const uint32_t g = (uint32_t)P.occ_grid;
+        const uint32_t cell = ((uint32_t)c2 * g + (uint32_t)c1) * g + (uint32_t)c0;
+        occ = (__ldg(P.canon_bits + (cell >> 5)) >> (cell & 31)) & 1u;
+      }
+      const unsigned word = __ballot_sync(0xffffffffu, occ);
+      if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(out)[j >> 5] = word;
+      continue;
+    }
     if (P.res_enabled) {
       pos_enc(P, s0, s1, s2, gcol, stride);
       float r0, r1, r2;
@@ -144,6 +199,28 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
       q[8] = cr; q[9] = cg; q[10] = cb; q[11] = sigma;
     }
   }
+}
+
+// Launches the FP32 kernel in kModeDensity or kModePose over P.occ_grid^3 cells,
+// writing occ_grid^3 / 32 words to bits.
+nr_status launch_occupancy_field(const FieldParams &P, int mode, uint32_t *bits, int device, cudaStream_t st) {
+  const size_t smem = field_f32_smem(P);
+  const uint32_t cells = (uint32_t)P.occ_grid * P.occ_grid * P.occ_grid;
+  const int blocks = std::min<int>(num_sms(device), (int)((cells + kF32Threads - 1) / kF32Threads));
+  if (mode == kModeDensity) {
+    NR_CHECK_CUDA(cudaFuncSetAttribute(field_f32_kernel<kModeDensity>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    field_f32_kernel<kModeDensity><<<blocks, kF32Threads, smem, st>>>(P, nullptr, 0, nullptr,
+                                                                       reinterpret_cast<float *>(bits));
+  } else {
+    NR_CHECK_CUDA(cudaFuncSetAttribute(field_f32_kernel<kModePose>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    field_f32_kernel<kModePose><<<blocks, kF32Threads, smem, st>>>(P, nullptr, 0, nullptr,
+                                                                    reinterpret_cast<float *>(bits));
+  }
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(1);
+  return NR_OK;
 }
 
 // --------------------------------------------------------------- composite
@@ -499,7 +576,8 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
              "nr_render: image size out of range");
   NR_REQUIRE(cam->n_samples >= 1 && cam->n_samples <= 1024, "nr_render: n_samples must be 1..1024");
   NR_REQUIRE(cam->fx != 0.f && cam->fy != 0.f, "nr_render: zero focal length");
-  NR_REQUIRE(!opts->use_occupancy || s->has_ellipsoids, "nr_render: occupancy requested but the subject has none");
+  NR_REQUIRE(!opts->use_occupancy || s->occ_source != kOccNone,
+             "nr_render: occupancy requested but the subject has none");
   if (!s->pose_set) {
     set_error("nr_render: call nr_set_pose first");
     return NR_ESTATE;
@@ -508,6 +586,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
+  if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;

@@ -10,6 +10,8 @@ namespace nr {
 
 constexpr int kModeRender = 0;   // input float4 (x, y, z, delta), output float4 (r, g, b, alpha)
 constexpr int kModeQuery = 1;    // input float3 points, output NR_QUERY_STRIDE floats per point
+constexpr int kModeDensity = 2;  // canonical cell centres: bit = sigma > occ_tau (FP32 tier only)
+constexpr int kModePose = 3;     // posed cell centres: bit = canonical cell of x_final set (FP32 tier only)
 constexpr int kCounters = 16;    // device counters per subject: live samples of each ray chunk
 
 struct CamParams {
@@ -112,6 +114,7 @@ nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t
 
 CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
+size_t field_f32_smem(const FieldParams &P);
 // mma_path for the bf16/f16 tiers: 0 = warp-level mma.sync over one 16-row m-tile per weight-fragment
 // read (16 warps/SM), 1 = tcgen05 (TMEM accumulators), 2 = mma.sync over two m-tiles per read (12 warps/SM).
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,

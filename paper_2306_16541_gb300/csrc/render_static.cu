@@ -72,7 +72,7 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
              "nr_render_static: mlp_dtype must be NR_F32, NR_BF16 or NR_F16");
   NR_REQUIRE(opts->feat_dtype == NR_F32 || opts->feat_dtype == NR_F16, "nr_render_static: bad feat_dtype");
   NR_REQUIRE(opts->t_min >= 0.f && opts->t_min < 1.f, "nr_render_static: t_min must be in [0, 1)");
-  NR_REQUIRE(!opts->use_occupancy || s->has_ellipsoids, "nr_render_static: the subject has no occupancy");
+  NR_REQUIRE(!opts->use_occupancy || s->occ_source != kOccNone, "nr_render_static: the subject has no occupancy");
   NR_REQUIRE(cam->width >= 1 && cam->height >= 1 && cam->n_samples >= 1 && cam->n_samples <= 1024,
              "nr_render_static: empty image or n_samples outside 1..1024");
   NR_REQUIRE(cam->fx != 0.f && cam->fy != 0.f, "nr_render_static: zero focal length");
@@ -97,6 +97,7 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
+  if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const CamParams C = cam_params(cam);
   MarchParams mp{};

@@ -173,7 +173,7 @@ static nr_status launch_request(nr_server *srv, Slot *sl, Request &q, DoneCtx *c
       cudaMemcpyAsync(sl->d_omega, sl->h_pose + kBones * 12, sizeof(float) * kBones * 3, cudaMemcpyHostToDevice, st));
   nr_status rc;
   if ((rc = launch_fold_bias(s, sl->d_omega, sl->d_bias1, 1, st)) != NR_OK) return rc;
-  if (r.opts.use_occupancy && (rc = launch_posed_bitfield(s, sl->d_G, sl->bits, st)) != NR_OK) return rc;
+  if (r.opts.use_occupancy && (rc = launch_posed_bitfield(s, sl->d_G, sl->d_bias1, sl->bits, st)) != NR_OK) return rc;
   FieldParams P = field_params(s, &r.opts);
   P.G = sl->d_G;
   P.bias1 = sl->d_bias1;
@@ -305,7 +305,7 @@ extern "C" nr_status nr_server_submit(nr_server *srv, const nr_request *req, uin
              "nr_server_submit: out_rgba must be device memory or pinned host memory");
   std::lock_guard<std::mutex> lock(srv->mu);
   NR_REQUIRE(req->subject < srv->subjects.size(), "nr_server_submit: unknown subject %u", req->subject);
-  NR_REQUIRE(!req->opts.use_occupancy || srv->subjects[req->subject]->has_ellipsoids,
+  NR_REQUIRE(!req->opts.use_occupancy || srv->subjects[req->subject]->occ_source != kOccNone,
              "nr_server_submit: occupancy requested for a subject without it");
   if (srv->stopping) {
     set_error("nr_server_submit: the server is stopping");

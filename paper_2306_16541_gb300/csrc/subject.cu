@@ -9,6 +9,7 @@
 #include <new>
 
 #include "field.cuh"
+#include "render.cuh"
 
 namespace nr {
 
@@ -391,13 +392,53 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   count_launches(launched + 1);
   s->params_dirty = false;
   s->bias_dirty = true;
+  s->occ_dirty = true;
   s->fp8_ready = false;
   s->t5_ready = false;
   (void)P;
   return NR_OK;
 }
 
-nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, uint32_t *bits, cudaStream_t st) {
+// Canonical occupancy dilated by r cells (Chebyshev distance, clipped at the
+// grid's faces): out(c) = OR of raw(c') over |c' - c|_inf <= r.  g^3 is a
+// multiple of the block, so every warp writes whole words.
+__global__ void __launch_bounds__(256) dilate_bits_kernel(const uint32_t *__restrict__ raw, int g, int r,
+                                                          uint32_t *__restrict__ out) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = (int)(c % g), y = (int)((c / g) % g), z = (int)(c / ((uint32_t)g * g));
+  bool occ = false;
+  for (int dz = -r; dz <= r && !occ; ++dz) {
+    const int zz = z + dz;
+    if (zz < 0 || zz >= g) continue;
+    for (int dy = -r; dy <= r && !occ; ++dy) {
+      const int yy = y + dy;
+      if (yy < 0 || yy >= g) continue;
+      for (int dx = -r; dx <= r; ++dx) {
+        const int xx = x + dx;
+        if (xx < 0 || xx >= g) continue;
+        const uint32_t q = ((uint32_t)zz * g + yy) * g + xx;
+        if ((__ldg(raw + (q >> 5)) >> (q & 31)) & 1u) {
+          occ = true;
+          break;
+        }
+      }
+    }
+  }
+  const unsigned word = __ballot_sync(0xffffffffu, occ);
+  if ((threadIdx.x & 31) == 0) out[c >> 5] = word;
+}
+
+nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const float *bias_dev, uint32_t *bits,
+                                cudaStream_t st) {
+  if (s->occ_source == kOccGrid) {
+    FieldParams P = field_params(s, nullptr);
+    P.G = G_dev;
+    P.bias1 = bias_dev;
+    P.occ_grid = (int)s->occ_grid;
+    P.occ_smin = s->occ_smin;
+    P.canon_bits = s->canon_bits;
+    return launch_occupancy_field(P, kModePose, bits, s->device, st);
+  }
   const int g = (int)s->occ_grid;
   const long n = (long)g * g * g;
   posed_bitfield_kernel<<<nblk(n, 256), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
@@ -412,6 +453,13 @@ nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *b
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
   return NR_OK;
+}
+
+nr_status ensure_occupancy(nr_subject *s, cudaStream_t st) {
+  if (s->occ_source != kOccGrid || !s->occ_dirty || !s->pose_set) return NR_OK;
+  nr_status r = launch_posed_bitfield(s, s->d_G, s->d_bias1, s->bits, st);
+  if (r == NR_OK) s->occ_dirty = false;
+  return r;
 }
 
 nr_status ensure_bias(nr_subject *s, cudaStream_t st) {
@@ -494,7 +542,7 @@ static void free_subject(nr_subject *s) {
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
-                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next};
+                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
@@ -518,8 +566,8 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   NR_REQUIRE(d->mlp_hidden_layers >= 1 && d->mlp_hidden_layers <= 4, "mlp_hidden_layers must be 1..4");
   NR_REQUIRE(!d->res_enabled || (d->res_params && d->res_pe_freqs <= 6), "residual MLP needs res_params, <=6 bands");
   NR_REQUIRE(d->wvol_res >= 2 && d->wvol_res <= 256, "wvol_res must be 2..256");
-  NR_REQUIRE(!d->ellipsoids || d->occ_grid == 32 || d->occ_grid == 64 || d->occ_grid == 128 || d->occ_grid == 256,
-             "occ_grid must be 32, 64, 128 or 256");
+  NR_REQUIRE(d->occ_grid == 0 || d->occ_grid == 32 || d->occ_grid == 64 || d->occ_grid == 128 || d->occ_grid == 256,
+             "occ_grid must be 32, 64, 128 or 256 (0 = 128)");
   for (int k = 0; k < 3; ++k) NR_REQUIRE(d->box_max[k] > d->box_min[k], "empty box");
   for (uint32_t i = 0; i < d->n_bones; ++i)
     NR_REQUIRE(d->parents[i] < (int32_t)i && d->parents[i] >= -1, "parents[%u] must be -1 or < %u", i, i);
@@ -551,6 +599,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   s->res_freqs = d->res_pe_freqs;
   s->occ_grid = d->occ_grid ? d->occ_grid : 128;
   s->has_ellipsoids = d->ellipsoids != nullptr;
+  s->occ_source = s->has_ellipsoids ? kOccEllipsoids : kOccNone;
   s->parents.assign(d->parents, d->parents + s->K);
   s->rest.assign(d->rest_joints, d->rest_joints + 3 * s->K);
 
@@ -645,7 +694,7 @@ extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *ro
   }
   NR_CHECK_CUDA(cudaMemcpyAsync(s->d_G, s->h_G, sizeof(float) * 12 * s->K, cudaMemcpyHostToDevice, st));
   NR_CHECK_CUDA(cudaMemcpyAsync(s->d_omega, s->h_omega, sizeof(float) * 3 * s->K, cudaMemcpyHostToDevice, st));
-  if (s->has_ellipsoids) {
+  if (s->occ_source == kOccEllipsoids) {
     const int g = (int)s->occ_grid;
     const long n = (long)g * g * g;
     posed_bitfield_kernel<<<nblk(n, 256), 256, 0, st>>>(s->d_G, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2],
@@ -653,6 +702,7 @@ extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *ro
     NR_CHECK_CUDA(cudaGetLastError());
     count_launches(1);
   }
+  s->occ_dirty = true;   // a canonical-grid source is posed lazily, after the bias fold
   // h_G / h_omega are reused by the next call: the copies must have read them
   NR_CHECK_CUDA(cudaStreamSynchronize(st));
   s->pose_set = true;
@@ -672,13 +722,79 @@ extern "C" nr_status nr_pose_transforms(nr_subject *s, float *G_out) {
 
 extern "C" nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out) {
   NR_REQUIRE(subject_ok(s) && bits_out, "nr_occupancy: bad argument");
-  if (!s->pose_set || !s->has_ellipsoids) {
-    set_error("nr_occupancy: no pose set or no ellipsoids");
+  if (!s->pose_set || s->occ_source == kOccNone) {
+    set_error("nr_occupancy: no pose set or no occupancy source");
+    return NR_ESTATE;
+  }
+  NR_CHECK_CUDA(cudaSetDevice(s->device));
+  nr_status r;
+  if ((r = prepare_params(s, nullptr)) != NR_OK) return r;
+  if ((r = ensure_bias(s, nullptr)) != NR_OK) return r;
+  if ((r = ensure_occupancy(s, nullptr)) != NR_OK) return r;
+  const size_t words = (size_t)s->occ_grid * s->occ_grid * s->occ_grid / 32;
+  NR_CHECK_CUDA(cudaMemcpy(bits_out, s->bits, words * 4, cudaMemcpyDeviceToHost));
+  return NR_OK;
+}
+
+// Allocates the canonical and posed grids of a kOccGrid source on first use.
+static nr_status grid_buffers(nr_subject *s) {
+  const size_t bytes = (size_t)s->occ_grid * s->occ_grid * s->occ_grid / 8;
+  if (!s->bits) NR_CHECK_CUDA(cudaMalloc(&s->bits, bytes));
+  if (!s->canon_bits) NR_CHECK_CUDA(cudaMalloc(&s->canon_bits, bytes));
+  if (!s->occ_raw) NR_CHECK_CUDA(cudaMalloc(&s->occ_raw, bytes));
+  return NR_OK;
+}
+
+extern "C" nr_status nr_refresh_occupancy(nr_subject *s, float sigma_threshold, uint32_t dilate, float s_min,
+                                          void *stream) {
+  NR_REQUIRE(subject_ok(s), "nr_refresh_occupancy: invalid handle");
+  NR_REQUIRE(isfinite(sigma_threshold) && sigma_threshold >= 0.f, "nr_refresh_occupancy: bad sigma_threshold");
+  NR_REQUIRE(dilate <= 3, "nr_refresh_occupancy: dilate must be 0..3");
+  NR_REQUIRE(isfinite(s_min) && s_min >= 0.f, "nr_refresh_occupancy: bad s_min");
+  NR_CHECK_CUDA(cudaSetDevice(s->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  nr_status r;
+  if ((r = grid_buffers(s)) != NR_OK) return r;
+  if ((r = prepare_params(s, st)) != NR_OK) return r;
+  FieldParams P = field_params(s, nullptr);
+  P.occ_grid = (int)s->occ_grid;
+  P.occ_tau = sigma_threshold;
+  if ((r = launch_occupancy_field(P, kModeDensity, s->occ_raw, s->device, st)) != NR_OK) return r;
+  const uint32_t cells = s->occ_grid * s->occ_grid * s->occ_grid;
+  dilate_bits_kernel<<<cells / 256, 256, 0, st>>>(s->occ_raw, (int)s->occ_grid, (int)dilate, s->canon_bits);
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(1);
+  s->occ_source = kOccGrid;
+  s->occ_smin = s_min;
+  s->occ_dirty = true;
+  return NR_OK;
+}
+
+extern "C" nr_status nr_set_canonical_occupancy(nr_subject *s, const uint32_t *bits, float s_min, void *stream) {
+  NR_REQUIRE(subject_ok(s) && bits, "nr_set_canonical_occupancy: bad argument");
+  NR_REQUIRE(isfinite(s_min) && s_min >= 0.f, "nr_set_canonical_occupancy: bad s_min");
+  NR_CHECK_CUDA(cudaSetDevice(s->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  nr_status r;
+  if ((r = grid_buffers(s)) != NR_OK) return r;
+  const size_t bytes = (size_t)s->occ_grid * s->occ_grid * s->occ_grid / 8;
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->canon_bits, bits, bytes, cudaMemcpyHostToDevice, st));
+  NR_CHECK_CUDA(cudaStreamSynchronize(st));   // the caller may free bits on return
+  s->occ_source = kOccGrid;
+  s->occ_smin = s_min;
+  s->occ_dirty = true;
+  return NR_OK;
+}
+
+extern "C" nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out) {
+  NR_REQUIRE(subject_ok(s) && bits_out, "nr_canonical_occupancy: bad argument");
+  if (s->occ_source != kOccGrid) {
+    set_error("nr_canonical_occupancy: the occupancy source is not a canonical grid");
     return NR_ESTATE;
   }
   NR_CHECK_CUDA(cudaSetDevice(s->device));
   const size_t words = (size_t)s->occ_grid * s->occ_grid * s->occ_grid / 32;
-  NR_CHECK_CUDA(cudaMemcpy(bits_out, s->bits, words * 4, cudaMemcpyDeviceToHost));
+  NR_CHECK_CUDA(cudaMemcpy(bits_out, s->canon_bits, words * 4, cudaMemcpyDeviceToHost));
   return NR_OK;
 }
 

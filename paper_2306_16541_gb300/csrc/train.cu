@@ -59,6 +59,7 @@ struct TrainDev {
   const uint32_t *frame_id, *px, *py;
   const float *target;
   uint32_t n_rays, S;
+  float loss_weight;      // lambda_mse
   uint64_t seed;
   float bg[3];
   const Frame *cams;
@@ -181,8 +182,8 @@ __global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
     }
     const float C0 = fmaf(Tr, T.bg[0], c0), C1 = fmaf(Tr, T.bg[1], c1), C2 = fmaf(Tr, T.bg[2], c2);
     const float e0 = C0 - T.target[3 * r], e1 = C1 - T.target[3 * r + 1], e2 = C2 - T.target[3 * r + 2];
-    lsum = e0 * e0 + e1 * e1 + e2 * e2;
-    const float scale = 2.f / (3.f * (float)T.n_rays);
+    lsum = T.loss_weight * (e0 * e0 + e1 * e1 + e2 * e2);
+    const float scale = 2.f * T.loss_weight / (3.f * (float)T.n_rays);
     const float g0 = scale * e0, g1 = scale * e1, g2 = scale * e2;
     float B = T.bg[0] * g0 + T.bg[1] * g1 + T.bg[2] * g2;
     for (int i = (int)cnt - 1; i >= 0; --i) {
@@ -664,6 +665,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
              "nr_train_step: bad Adam hyper-parameters");
   for (int k = 0; k < 4; ++k) NR_REQUIRE(b->lr_scale[k] >= 0.f, "nr_train_step: negative lr_scale");
+  NR_REQUIRE(b->loss_weight >= 0.f, "nr_train_step: negative loss_weight");
   if (s->n_frames == 0) {
     set_error("nr_train_step: call nr_set_frames first");
     return NR_ESTATE;
@@ -722,6 +724,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.target = b->target_rgb;
   T.n_rays = b->n_rays;
   T.S = b->n_samples;
+  T.loss_weight = b->loss_weight > 0.f ? b->loss_weight : 1.f;
   T.seed = b->step_seed;
   for (int k = 0; k < 3; ++k) T.bg[k] = b->bg[k];
   T.cams = s->f_cam;

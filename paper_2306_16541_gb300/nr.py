@@ -27,6 +27,7 @@ NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES = range(4)
 # Per-group learning-rate multipliers (weight volume, hash, canonical MLP, residual MLP):
 # Sec. 5.2 uses a 10x smaller rate for the networks other than the NeRF network.
 PAPER_LR_SCALE = (0.1, 1.0, 1.0, 0.1)
+PAPER_MSE_WEIGHT = 0.2      # lambda_mse of Sec. 5.2
 NR_QUERY_STRIDE = 12
 NR_RENDER_PROFILE = 1
 NR_RENDER_TCGEN05 = 2
@@ -68,7 +69,7 @@ class nr_train_batch(C.Structure):
                 ("target_rgb", _fp), ("n_samples", C.c_uint32), ("bg", C.c_float * 3),
                 ("step_seed", C.c_uint64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("hann_alpha", C.c_float), ("flags", C.c_uint32),
-                ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4)]
+                ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4), ("loss_weight", C.c_float)]
 
 
 class nr_request(C.Structure):
@@ -100,6 +101,9 @@ def _load() -> C.CDLL:
         "nr_params_changed": ([vp], C.c_int),
         "nr_pose_transforms": ([vp, _fp], C.c_int),
         "nr_occupancy": ([vp, _up], C.c_int),
+        "nr_refresh_occupancy": ([vp, C.c_float, C.c_uint32, C.c_float, vp], C.c_int),
+        "nr_set_canonical_occupancy": ([vp, _up, C.c_float, vp], C.c_int),
+        "nr_canonical_occupancy": ([vp, _up], C.c_int),
         "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
@@ -289,6 +293,27 @@ def nr_occupancy(h, grid: int = 128) -> np.ndarray:
     return bits
 
 
+OCC_S_MIN = 1e-3   # default least bone-weight sum of a posed occupancy cell
+
+
+def nr_refresh_occupancy(h, sigma_threshold: float, dilate: int = 1, s_min: float = OCC_S_MIN,
+                         stream=None) -> None:
+    check(lib.nr_refresh_occupancy(h, float(sigma_threshold), int(dilate), float(s_min), _stream(stream)),
+          "nr_refresh_occupancy")
+
+
+def nr_set_canonical_occupancy(h, bits, s_min: float = OCC_S_MIN, stream=None) -> None:
+    b = np.ascontiguousarray(bits, np.uint32)
+    check(lib.nr_set_canonical_occupancy(h, _ptr(b, C.c_uint32), float(s_min), _stream(stream)),
+          "nr_set_canonical_occupancy")
+
+
+def nr_canonical_occupancy(h, grid: int = 128) -> np.ndarray:
+    bits = np.zeros(grid ** 3 // 32, np.uint32)
+    check(lib.nr_canonical_occupancy(h, _ptr(bits, C.c_uint32)), "nr_canonical_occupancy")
+    return bits
+
+
 class Subject:
     """One performer resident on the GPU (owns an nr_subject handle)."""
 
@@ -319,7 +344,7 @@ class Subject:
     def train_step(self, frame_id, px, py, target_rgb, n_samples: int, step_seed: int, lr: float = 1e-2,
                    betas=(0.9, 0.99), eps: float = 1e-8, bg=(0.0, 0.0, 0.0), hann_alpha: float = -1.0,
                    grad_only: bool = False, train_mask: int = 0, lr_scale=(0.0, 0.0, 0.0, 0.0),
-                   stream=None) -> float:
+                   loss_weight: float = 0.0, stream=None) -> float:
         b = nr_train_batch()
         b.n_rays = int(frame_id.shape[0])
         b.frame_id = C.cast(C.c_void_p(frame_id.data_ptr()), _up)
@@ -331,6 +356,7 @@ class Subject:
         b.lr, b.beta1, b.beta2, b.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
         b.hann_alpha, b.flags, b.train_mask = float(hann_alpha), NR_GRAD_ONLY if grad_only else 0, int(train_mask)
         b.lr_scale[:] = [float(v) for v in lr_scale]
+        b.loss_weight = float(loss_weight)
         return nr_train_step(self.h, b, stream)
 
     def param(self, which: int):
@@ -347,6 +373,15 @@ class Subject:
 
     def occupancy(self):
         return nr_occupancy(self.h, self.occ_grid)
+
+    def refresh_occupancy(self, sigma_threshold: float, dilate: int = 1, s_min: float = OCC_S_MIN, stream=None):
+        nr_refresh_occupancy(self.h, sigma_threshold, dilate, s_min, stream)
+
+    def set_canonical_occupancy(self, bits, s_min: float = OCC_S_MIN, stream=None):
+        nr_set_canonical_occupancy(self.h, bits, s_min, stream)
+
+    def canonical_occupancy(self):
+        return nr_canonical_occupancy(self.h, self.occ_grid)
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -347,6 +347,58 @@ def subject(seed: int, *, vol_res: int = 32, hash_levels: int = 8, log2_t: int =
     return d
 
 
+def shaped_density(subj: dict, beta: float = 8.0, bias: float = -4.0, keep_ellipsoids: bool = False) -> dict:
+    """A copy of `subj` (made with ellipsoids) whose canonical density follows the performer's body.
+
+    The finest dense hash level holds, in feature 0, f(v) = clip(1 - min_i q_i(v), -1, 1) at each
+    vertex v, q_i the normalised squared radius of v in canonical ellipsoid i (positive inside
+    the body, negative away from it).  The canonical MLP is rewired so that hidden units 0 and 1
+    carry relu(f) and relu(-f) through every layer and o_3 = beta (relu(f) - relu(-f)) + bias =
+    beta f + bias: sigma = softplus(beta f + bias) is ~softplus(beta + bias) inside the body and
+    ~softplus(-beta + bias) away from it.  Colour keeps the random weights on the other units.
+    """
+    d = dict(subj)
+    levels = [int(n) for n in d["level_res"]]
+    T = 1 << int(d["log2_T"])
+    dense = [l for l, n in enumerate(levels) if (n + 1) ** 3 <= T]
+    lv = dense[-1]
+    n = levels[lv]
+    iz, iy, ix = np.meshgrid(np.arange(n + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    bmin, bmax = np.asarray(d["box_min"], np.float64), np.asarray(d["box_max"], np.float64)
+    v = bmin + np.stack([ix.ravel(), iy.ravel(), iz.ravel()], 1) / n * (bmax - bmin)
+    E = np.asarray(subj["ellipsoids"], np.float64)
+    q = np.full(v.shape[0], np.inf)
+    for e in E:
+        loc = (v - e[:3]) @ e[3:12].reshape(3, 3).T / e[12:15]
+        q = np.minimum(q, (loc ** 2).sum(1))
+    f = np.clip(1.0 - q, -1.0, 1.0)
+    tab = np.array(d["hash_table"], np.float32, copy=True)
+    idx = ix.ravel() + iy.ravel() * (n + 1) + iz.ravel() * (n + 1) ** 2
+    tab[lv, idx, 0] = f.astype(np.float32)
+    d["hash_table"] = tab
+    layers = [(np.array(W, np.float32, copy=True), np.array(b, np.float32, copy=True)) for W, b in d["mlp_layers"]]
+    k = 2 * lv
+    W, b = layers[0]
+    W[0:2, :] = 0.0
+    W[0, k], W[1, k] = 1.0, -1.0
+    b[0:2] = 0.0
+    for W, b in layers[1:-1]:
+        W[0:2, :] = 0.0
+        W[:, 0:2] = 0.0
+        W[0, 0] = W[1, 1] = 1.0
+        b[0:2] = 0.0
+    W, b = layers[-1]
+    W[:, 0:2] = 0.0
+    W[3, :] = 0.0
+    W[3, 0], W[3, 1] = beta, -beta
+    b[3] = bias
+    d["mlp_layers"] = layers
+    d["mlp_params"] = pack_layers(layers)
+    if not keep_ellipsoids:
+        d.pop("ellipsoids", None)
+    return d
+
+
 def config_tiny(seed: int = 1234) -> dict:
     """64x64 image, fx=fy=80, 32 samples in [1.5, 3.5] m, no occupancy skip,
     32^3x25 volume, 8x2 hash levels of 2^14 entries (N 16..256), MLP 32-64-64-4, FP32."""
@@ -396,6 +448,24 @@ def pixel_batch(seed: int, n_rays: int, n_frames: int, width: int, height: int) 
     return dict(frame=rng.integers(0, n_frames, n_rays).astype(np.uint32),
                 px=rng.integers(0, width, n_rays).astype(np.uint32),
                 py=rng.integers(0, height, n_rays).astype(np.uint32))
+
+
+def patch_batch(seed: int, frames, n_images: int, n_patches: int = 6, size: int = 20,
+                width: int = 512, height: int = 512) -> dict:
+    """Patch-based ray batch (Sec. 5.2: 6 patches of 20 x 20 pixels per image): n_images frames
+    drawn from `frames` (a count), each contributing n_patches square patches at random positions."""
+    rng = np.random.default_rng(seed)
+    fr, px, py = [], [], []
+    yy, xx = np.meshgrid(np.arange(size), np.arange(size), indexing="ij")
+    for f in rng.integers(0, frames, n_images):
+        for _ in range(n_patches):
+            x0 = int(rng.integers(0, width - size + 1))
+            y0 = int(rng.integers(0, height - size + 1))
+            fr.append(np.full(size * size, f))
+            px.append((x0 + xx).ravel())
+            py.append((y0 + yy).ravel())
+    return dict(frame=np.concatenate(fr).astype(np.uint32), px=np.concatenate(px).astype(np.uint32),
+                py=np.concatenate(py).astype(np.uint32))
 
 
 def request_stream(seed: int, n_subjects: int, rate_hz: float, duration_s: float,

@@ -49,7 +49,7 @@ def _setup(n_rays=384, n_frames=3, res=32, S=16, seed=31):
     return subj, frames, batch, tgt
 
 
-def _gpu_step(subj, frames, batch, tgt, S, seed, grad_only, lr=1e-2, train_mask=0):
+def _gpu_step(subj, frames, batch, tgt, S, seed, grad_only, lr=1e-2, train_mask=0, loss_weight=0.0):
     nr = nrmod()
     Sub = nr.Subject(subj)
     try:
@@ -57,7 +57,7 @@ def _gpu_step(subj, frames, batch, tgt, S, seed, grad_only, lr=1e-2, train_mask=
         before = {g: Sub.param(i)[0].clone() for i, g in enumerate(GROUPS)}
         loss = Sub.train_step(u32(batch["frame"]), u32(batch["px"]), u32(batch["py"]),
                               torch.from_numpy(np.ascontiguousarray(tgt, np.float32)).cuda(), S, seed,
-                              lr=lr, grad_only=grad_only, train_mask=train_mask)
+                              lr=lr, grad_only=grad_only, train_mask=train_mask, loss_weight=loss_weight)
         torch.cuda.synchronize()
         grads = {g: Sub.param(i)[1].cpu().numpy().astype(np.float64) for i, g in enumerate(GROUPS)}
         after = {g: Sub.param(i)[0].cpu().numpy().astype(np.float64) for i, g in enumerate(GROUPS)}
@@ -67,9 +67,9 @@ def _gpu_step(subj, frames, batch, tgt, S, seed, grad_only, lr=1e-2, train_mask=
         Sub.close()
 
 
-def _oracle_grads(subj, frames, batch, tgt, S, seed):
+def _oracle_grads(subj, frames, batch, tgt, S, seed, loss_weight=1.0):
     P = OF.Params(subj, requires_grad=True)
-    loss, _ = OR.train_loss(subj, P, frames, batch, tgt, seed, S, np.zeros(3))
+    loss, _ = OR.train_loss(subj, P, frames, batch, tgt, seed, S, np.zeros(3), loss_weight=loss_weight)
     loss.backward()
     g = {"wvol": P.wvol.grad.numpy().ravel(), "table": P.table.grad.numpy().ravel()}
     g["mlp"] = np.concatenate([np.concatenate([W.grad.numpy().ravel(), b.grad.numpy().ravel()]) for W, b in P.mlp])
@@ -166,3 +166,26 @@ def test_train_mask_freezes_groups():
                                     train_mask=nr.NR_TRAIN_HASH | nr.NR_TRAIN_MLP)
     assert np.array_equal(before["wvol"], after["wvol"]) and np.array_equal(before["res"], after["res"])
     assert not np.array_equal(before["table"], after["table"]) and not np.array_equal(before["mlp"], after["mlp"])
+
+
+def test_patch_batch_with_weighted_mse():
+    """Sec. 5.2 batch layout: 6 patches of 20 x 20 pixels per image, the MSE term
+    weighted by lambda_mse = 0.2; loss and gradients against the oracle on the
+    kink-free linear-table field (2400 contiguous rays put many samples near
+    the same cell faces, where float32 and float64 may pick different cells)."""
+    nr = nrmod()
+    subj = _linear_table(synth.subject(71, hash_scale=0.5))
+    frames = synth.training_frames(72, 4, res=48)
+    for c in frames["cameras"]:
+        c.n_samples = 16
+    batch = synth.patch_batch(73, 4, n_images=1, width=48, height=48)
+    n = batch["frame"].shape[0]
+    assert n == 6 * 400
+    tgt = np.random.default_rng(74).uniform(0, 1, size=(n, 3)).astype(np.float32)
+    loss, grads, _, _ = _gpu_step(subj, frames, batch, tgt, 16, 19, grad_only=True,
+                                  loss_weight=nr.PAPER_MSE_WEIGHT)
+    ref_loss, ref = _oracle_grads(subj, frames, batch, tgt, 16, 19, loss_weight=nr.PAPER_MSE_WEIGHT)
+    assert abs(loss - ref_loss) <= 1e-5 * max(1.0, ref_loss), (loss, ref_loss)
+    for g in ("wvol", "table", "mlp"):
+        assert np.linalg.norm(ref[g]) > 0, g
+        assert _rel(grads[g], ref[g]) <= 1e-4, (g, _rel(grads[g], ref[g]))
