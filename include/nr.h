@@ -125,9 +125,28 @@ nr_status nr_destroy(nr_subject *s);
  * some bone i the canonical image G_i(c) of its centre lies in ellipsoid i
  * dilated by half a cell diagonal.  With NR_POSE_MATRICES, axis_angle is
  * G[n_bones][12] float32 and used as given; the joint angles are then taken
- * as zero for the residual MLP.  Host pointers. */
+ * as zero for the residual MLP.  With a pose refiner installed
+ * (nr_set_pose_refiner) and joint angles given, G is that of the refined pose,
+ * computed on the device, and is re-derived after every training step that
+ * updates the refiner.  Host pointers. */
 nr_status nr_set_pose(nr_subject *s, const float *axis_angle, const float *root_t,
                       uint32_t flags, void *stream);
+
+/* Pose refiner (Sec. 4.1): Delta_Omega = MLP_theta(Omega) corrects the
+ * estimated joint angles before forward kinematics.  MLP_theta sees the
+ * 3 (n_bones - 1) = 69 angles of the non-root joints and returns one
+ * axis-angle correction per non-root joint; hidden_layers (1..4) ReLU layers
+ * of `width` (1..256) units, then a linear layer to 69.  params (host) packs,
+ * per layer, W[out][in] row-major then b[out] (69 -> width, width -> width,
+ * ..., width -> 69).  The refined local rotation of joint j >= 1 is
+ * Rot(Delta_omega_j) Rot(omega_j); the root keeps its estimate; the residual
+ * MLP stays conditioned on the estimated angles.  Training (nr_train_step)
+ * then back-propagates dL/dG_i of every frame, reduced over the batch's
+ * samples, through the kinematic chain into MLP_theta (Adam group
+ * NR_TRAIN_REFINER, parameters NR_PARAM_REFINER).  params == NULL switches
+ * the refiner off.  The Adam moments restart at each call. */
+nr_status nr_set_pose_refiner(nr_subject *s, uint32_t width, uint32_t hidden_layers, const float *params,
+                              void *stream);
 
 /* Pinhole camera, OpenCV convention (x right, y down, z forward).
  * Pixel (u, v) looks along R^T ((u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1)
@@ -207,7 +226,8 @@ nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float *axis_angl
 #define NR_TRAIN_HASH 2u
 #define NR_TRAIN_MLP 4u
 #define NR_TRAIN_RES 8u
-#define NR_TRAIN_ALL 15u
+#define NR_TRAIN_REFINER 16u
+#define NR_TRAIN_ALL 31u
 
 /* One training batch of pixel rays.  frame_id, px, py: device uint32[n];
  * target_rgb: device float32[n][3].  Samples are stratified: bin i of the
@@ -230,6 +250,7 @@ typedef struct {
                                     the NeRF network with a 10x larger rate than the others. */
   float loss_weight;             /* lambda_mse: L = lambda_mse * MSE (Sec. 5.2 uses 0.2 beside
                                     LPIPS); 0 means 1 */
+  float lr_scale_refiner;        /* lr multiplier of the pose refiner; 0 means 1 */
 } nr_train_batch;
 
 /* Forward, loss L = loss_weight * mean over rays and channels of (C^ - C_gt)^2, the
@@ -243,6 +264,7 @@ nr_status nr_train_step(nr_subject *s, const nr_train_batch *batch, float *loss_
 #define NR_PARAM_HASH 1u    /* [L][T][F] (float32 master copy) */
 #define NR_PARAM_MLP 2u     /* canonical MLP, packed as in the descriptor */
 #define NR_PARAM_RES 3u     /* residual MLP, packed as in the descriptor */
+#define NR_PARAM_REFINER 4u /* pose refiner MLP_theta, packed as in nr_set_pose_refiner */
 /* Device pointers of a parameter group (float32) and of its gradient buffer,
  * and its element count.  Writing the parameters through *dev_ptr is allowed
  * between calls; call nr_params_changed() afterwards. */

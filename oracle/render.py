@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import decide32, fk, rng
+from . import decide32, fk, refine, rng
 from .field import F64, Params, field, t64
 
 
@@ -86,15 +86,20 @@ def sample_alpha(out, delta, live):
     return torch.where(keep, a, torch.zeros((), dtype=F64))
 
 
-def pose_inputs(subj: dict, axis_angle, root_t):
-    """FP64 G (R [K,3,3], t [K,3]) and the flattened joint angles Omega^o [3K]."""
+def pose_inputs(subj: dict, axis_angle, root_t, refiner=None):
+    """FP64 G (R [K,3,3], t [K,3]) and the flattened joint angles Omega [3K] that condition
+    MLP_res; with `refiner` (MLP_theta layers, Sec. 4.1) G is that of the refined pose."""
+    omega = t64(np.asarray(axis_angle, np.float32)).reshape(-1)
+    if refiner is not None:
+        R, t = refine.refined_transforms(subj["parents"], subj["rest_joints"], axis_angle, root_t, refiner)
+        return R, t, omega
     R, t = fk.bone_transforms(subj["parents"], subj["rest_joints"], axis_angle, root_t)
-    return torch.from_numpy(R), torch.from_numpy(t), t64(np.asarray(axis_angle, np.float32)).reshape(-1)
+    return torch.from_numpy(R), torch.from_numpy(t), omega
 
 
 def render_pixels(subj: dict, P: Params, pose, cam, px, py, use_occupancy: bool,
                   grid: int = 128, chunk: int = 1024, alpha=None, return_counts: bool = False,
-                  bits=None):
+                  bits=None, refiner=None):
     """RGBA [N][4] (float64) of pixels (px, py) for one pose and camera.
 
     The box-hit and occupancy decisions come from `decide32` (float32, the
@@ -102,7 +107,7 @@ def render_pixels(subj: dict, P: Params, pose, cam, px, py, use_occupancy: bool,
     grid^3 posed bitfield) replaces the ellipsoid bitfield when given.
     """
     axis_angle, root_t = pose
-    G_R, G_t, omega = pose_inputs(subj, axis_angle, root_t)
+    G_R, G_t, omega = pose_inputs(subj, axis_angle, root_t, refiner)
     px = np.asarray(px)
     py = np.asarray(py)
     o32, d32 = decide32.ray_dirs32(cam, px, py)
@@ -150,9 +155,11 @@ def render_image(subj: dict, pose, cam, use_occupancy: bool, **kw) -> torch.Tens
 
 
 def train_loss(subj: dict, P: Params, frames: dict, batch: dict, target_rgb, step_seed: int,
-               n_samples: int, bg, alpha=None, ray_offset: int = 0, loss_weight: float = 1.0):
+               n_samples: int, bg, alpha=None, ray_offset: int = 0, loss_weight: float = 1.0,
+               refiner=None):
     """loss_weight x mean squared error over rays and channels of one training batch (no
-    occupancy, no ERT); Sec. 5.2 weights the MSE term by lambda_mse = 0.2.
+    occupancy, no ERT); Sec. 5.2 weights the MSE term by lambda_mse = 0.2.  `refiner`
+    (MLP_theta layers) corrects each frame's pose (Sec. 4.1).
 
     frames: axis_angle [F][24][3], root_t [F][3], cameras [F]; batch: frame, px, py [N].
     """
@@ -168,7 +175,7 @@ def train_loss(subj: dict, P: Params, frames: dict, batch: dict, target_rgb, ste
     for f in np.unique(fr):
         sel = np.nonzero(fr == f)[0]
         cam = frames["cameras"][f]
-        G_R, G_t, omega = pose_inputs(subj, frames["axis_angle"][f], frames["root_t"][f])
+        G_R, G_t, omega = pose_inputs(subj, frames["axis_angle"][f], frames["root_t"][f], refiner)
         o32, d32 = decide32.ray_dirs32(cam, px[sel], py[sel])
         _, _, hit32 = decide32.clip32(o32, d32, cam.t_near, cam.t_far, subj["box_min"], subj["box_max"])
         o, d = rays64(cam, px[sel], py[sel])

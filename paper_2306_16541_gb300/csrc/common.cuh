@@ -153,10 +153,13 @@ struct nr_subject {
   bool t5_ready = false;
   // current pose
   bool pose_set = false;
-  float h_G[24 * 12];
+  bool pose_matrices = false;        // the pose was given as G (NR_POSE_MATRICES)
+  bool pose_dirty = false;           // d_G (and the posed bitfield) must be re-derived
+  float h_G[24 * 12];                // host forward kinematics of the estimated pose
   float h_omega[24 * 3];
+  float h_root[3] = {0.f, 0.f, 0.f};
   float *d_G = nullptr;              // [24][12]
-  float *d_omega = nullptr;          // [72]
+  float *d_omega = nullptr;          // [72] joint angles, then [3] root translation
   float *d_bias1 = nullptr;          // [64]
   bool bias_dirty = true;
   float *ellip = nullptr;            // [24][15]
@@ -165,8 +168,18 @@ struct nr_subject {
   uint32_t *occ_raw = nullptr;       // occ_grid^3 / 32, undilated density test
   float occ_smin = 0.f;              // least bone-weight sum of a posed cell (kOccGrid)
   bool occ_dirty = false;            // posed grid stale (kOccGrid)
+  // pose refiner MLP_theta (Sec. 4.1); ref_layers == 0: off
+  uint32_t ref_width = 0, ref_layers = 0;
+  float *ref = nullptr, *g_ref = nullptr, *ref_m = nullptr, *ref_v = nullptr;
+  size_t n_ref = 0;
+  uint32_t ref_t = 0;                // Adam steps of the refiner
   // training frames
   uint32_t n_frames = 0, frames_cap = 0;
+  std::vector<float> h_fG;           // host forward kinematics of the estimated frame poses
+  bool fG_refined = false;           // f_G holds refined poses
+  float *f_root = nullptr;           // [F][3]
+  float *f_dG = nullptr;             // [F][24][12] dL/dG (refiner)
+  size_t f_dG_cap = 0;
   float *f_G = nullptr;              // [F][24][12]
   float *f_omega = nullptr;          // [F][72]
   float *f_bias1 = nullptr;          // [F][64]
@@ -218,6 +231,12 @@ constexpr uint32_t kOccNone = 0, kOccEllipsoids = 1, kOccGrid = 2;   // nr_subje
 nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const float *bias_dev, uint32_t *bits,
                                 cudaStream_t st);
 nr_status ensure_occupancy(nr_subject *s, cudaStream_t st);    // posed grid of the current pose (kOccGrid)
+nr_status ensure_pose(nr_subject *s, cudaStream_t st);         // d_G (refined if MLP_theta is on), bitfields
+nr_status launch_refine_fk(const nr_subject *s, const float *omega, int omega_stride, const float *root,
+                           int root_stride, int n, float *G, cudaStream_t st);
+nr_status launch_refine_bwd(const nr_subject *s, const float *omega, int omega_stride, const float *root,
+                            int root_stride, int n, const float *dG, float *g, cudaStream_t st);
+size_t refiner_param_count(uint32_t width, uint32_t layers);
 nr_status launch_occupancy_field(const FieldParams &P, int mode, uint32_t *bits, int device, cudaStream_t st);
 nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *bias_dev, int n_poses, cudaStream_t st);
 bool subject_ok(const nr_subject *s);

@@ -34,6 +34,29 @@ __device__ __forceinline__ float trilinear_quad(const float4 *__restrict__ q, in
   return fmaf(fz, z1 - z0, z0);
 }
 
+// The same trilinear sample and its gradient d/d(ux, uy, uz) inside the cell
+// (one-sided on a cell face: the cell is the floor of u, as in the value).
+__device__ __forceinline__ float trilinear_quad_grad(const float4 *__restrict__ q, int R, float ux, float uy, float uz,
+                                                     float &gx, float &gy, float &gz) {
+  gx = gy = gz = 0.f;
+  const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
+  const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+  if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) return 0.f;
+  const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
+  const int R1 = R + 1;
+  const int b = ((iz + 1) * R1 + (iy + 1)) * R1 + (ix + 1);
+  const float4 a = __ldg(q + b), c = __ldg(q + b + R1 * R1);
+  const float a0 = fmaf(fx, a.y - a.x, a.x), a1 = fmaf(fx, a.w - a.z, a.z);
+  const float c0 = fmaf(fx, c.y - c.x, c.x), c1 = fmaf(fx, c.w - c.z, c.z);
+  const float z0 = fmaf(fy, a1 - a0, a0), z1 = fmaf(fy, c1 - c0, c0);
+  const float ex0 = fmaf(fy, (a.w - a.z) - (a.y - a.x), a.y - a.x);   // d/dfx on the z0 face
+  const float ex1 = fmaf(fy, (c.w - c.z) - (c.y - c.x), c.y - c.x);   // d/dfx on the z1 face
+  gx = fmaf(fz, ex1 - ex0, ex0);
+  gy = fmaf(fz, (c1 - c0) - (a1 - a0), a1 - a0);
+  gz = z1 - z0;
+  return fmaf(fz, z1 - z0, z0);
+}
+
 __host__ __device__ inline size_t quad_channel(int R) { return (size_t)(R + 2) * (R + 1) * (R + 1); }
 
 // sG: the 24 bone transforms [24][12] (rows [R | t]) in shared memory.

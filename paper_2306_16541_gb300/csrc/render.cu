@@ -585,6 +585,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   NR_CHECK_CUDA(cudaSetDevice(s->device));
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
+  if ((r = ensure_pose(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
@@ -690,6 +691,7 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   NR_CHECK_CUDA(cudaSetDevice(s->device));
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
+  if ((r = ensure_pose(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);

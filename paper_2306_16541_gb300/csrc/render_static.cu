@@ -96,6 +96,7 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
   if (r != NR_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
+  if ((r = ensure_pose(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);

@@ -44,7 +44,7 @@ struct Slot {
   float *d_G = nullptr, *d_omega = nullptr, *d_bias1 = nullptr;
   uint32_t *bits = nullptr;
   FrameWork w{};
-  float *h_pose = nullptr;          // pinned: G [24*12] then omega [72]
+  float *h_pose = nullptr;          // pinned: G [24*12], omega [72], root translation [3]
   size_t bytes = 0;
   bool busy = false;
   uint64_t req = 0;
@@ -120,7 +120,7 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
     return fail(e, "slot allocation " #p);
   if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
   SLOT_ALLOC(sl->d_G, kBones * 12 * sizeof(float));
-  SLOT_ALLOC(sl->d_omega, kBones * 3 * sizeof(float));
+  SLOT_ALLOC(sl->d_omega, (kBones * 3 + 3) * sizeof(float));
   SLOT_ALLOC(sl->d_bias1, kWidth * sizeof(float));
   SLOT_ALLOC(sl->bits, (size_t)grid * grid * grid / 8);
   SLOT_ALLOC(sl->w.samp, kSlotSamples * sizeof(float4));
@@ -130,7 +130,7 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
   SLOT_ALLOC(sl->w.state, kSlotRays * sizeof(float4));
   SLOT_ALLOC(sl->w.next, kSlotRays * sizeof(uint32_t));
 #undef SLOT_ALLOC
-  if ((e = cudaMallocHost((void **)&sl->h_pose, (kBones * 12 + kBones * 3) * sizeof(float))) != cudaSuccess)
+  if ((e = cudaMallocHost((void **)&sl->h_pose, (kBones * 12 + kBones * 3 + 3) * sizeof(float))) != cudaSuccess)
     return fail(e, "pinned pose buffer");
   sl->w.cap_samples = kSlotSamples;
   sl->w.cap_rays = kSlotRays;
@@ -166,12 +166,18 @@ static nr_status launch_request(nr_server *srv, Slot *sl, Request &q, DoneCtx *c
   const nr_request &r = q.r;
   nr_subject *s = srv->subjects[r.subject];
   cudaStream_t st = sl->stream;
-  forward_kinematics(s, r.axis_angle, r.root_t, sl->h_pose);
   memcpy(sl->h_pose + kBones * 12, r.axis_angle, sizeof(float) * kBones * 3);
-  NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_G, sl->h_pose, sizeof(float) * kBones * 12, cudaMemcpyHostToDevice, st));
-  NR_CHECK_CUDA(
-      cudaMemcpyAsync(sl->d_omega, sl->h_pose + kBones * 12, sizeof(float) * kBones * 3, cudaMemcpyHostToDevice, st));
+  memcpy(sl->h_pose + kBones * 15, r.root_t, sizeof(float) * 3);
+  NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_omega, sl->h_pose + kBones * 12, sizeof(float) * (kBones * 3 + 3),
+                                cudaMemcpyHostToDevice, st));
   nr_status rc;
+  if (s->ref_layers) {   // the refined pose (Sec. 4.1), on the device
+    if ((rc = launch_refine_fk(s, sl->d_omega, 3 * kBones, sl->d_omega + 3 * kBones, 3, 1, sl->d_G, st)) != NR_OK)
+      return rc;
+  } else {
+    forward_kinematics(s, r.axis_angle, r.root_t, sl->h_pose);
+    NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_G, sl->h_pose, sizeof(float) * kBones * 12, cudaMemcpyHostToDevice, st));
+  }
   if ((rc = launch_fold_bias(s, sl->d_omega, sl->d_bias1, 1, st)) != NR_OK) return rc;
   if (r.opts.use_occupancy && (rc = launch_posed_bitfield(s, sl->d_G, sl->d_bias1, sl->bits, st)) != NR_OK) return rc;
   FieldParams P = field_params(s, &r.opts);

@@ -542,7 +542,8 @@ static void free_subject(nr_subject *s) {
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
-                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw};
+                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
+                  s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
@@ -635,7 +636,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->tc_bf16, (size_t)s->tlay.total * 2);
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
   ALLOC(s->d_G, kBones * 12 * 4);
-  ALLOC(s->d_omega, kBones * 3 * 4);
+  ALLOC(s->d_omega, (kBones * 3 + 3) * 4);
   ALLOC(s->d_bias1, kWidth * 4);
   ALLOC(s->counter, 16 * 4);
   if (s->has_ellipsoids) {
@@ -660,7 +661,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
     H2D(s->ellip, d->ellipsoids, kBones * 15 * 4);
   }
 #undef H2D
-  e = cudaMemsetAsync(s->d_omega, 0, kBones * 3 * 4, st);
+  e = cudaMemsetAsync(s->d_omega, 0, (kBones * 3 + 3) * 4, st);
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync omega");
   // the call's host arrays may be freed on return: finish the copies first
   e = cudaStreamSynchronize(st);
@@ -686,14 +687,38 @@ extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *ro
   if (flags & NR_POSE_MATRICES) {
     memcpy(s->h_G, aa, sizeof(float) * 12 * s->K);
     memset(s->h_omega, 0, sizeof(s->h_omega));
+    memset(s->h_root, 0, sizeof(s->h_root));
   } else {
     for (uint32_t i = 0; i < 3 * s->K; ++i)
       NR_REQUIRE(isfinite(aa[i]), "nr_set_pose: non-finite joint angle at %u", i);
     forward_kinematics(s, aa, root_t, s->h_G);
     memcpy(s->h_omega, aa, sizeof(float) * 3 * s->K);
+    for (int k = 0; k < 3; ++k) s->h_root[k] = root_t ? root_t[k] : 0.f;
   }
-  NR_CHECK_CUDA(cudaMemcpyAsync(s->d_G, s->h_G, sizeof(float) * 12 * s->K, cudaMemcpyHostToDevice, st));
+  s->pose_matrices = (flags & NR_POSE_MATRICES) != 0;
   NR_CHECK_CUDA(cudaMemcpyAsync(s->d_omega, s->h_omega, sizeof(float) * 3 * s->K, cudaMemcpyHostToDevice, st));
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->d_omega + 3 * s->K, s->h_root, sizeof(float) * 3, cudaMemcpyHostToDevice, st));
+  s->pose_set = true;
+  s->pose_dirty = true;
+  s->bias_dirty = true;
+  nr_status r = ensure_pose(s, st);
+  // h_G / h_omega / h_root are reused by the next call: the copies must have read them
+  NR_CHECK_CUDA(cudaStreamSynchronize(st));
+  return r;
+}
+
+// Derives the device transforms of the current pose: the refined pose when
+// MLP_theta is on (and the pose came as joint angles), else the host forward
+// kinematics; then the posed occupancy of the subject's source.
+nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
+  if (!s->pose_dirty || !s->pose_set) return NR_OK;
+  nr_status r;
+  if (s->ref_layers && !s->pose_matrices) {
+    if ((r = launch_refine_fk(s, s->d_omega, 3 * kBones, s->d_omega + 3 * kBones, 3, 1, s->d_G, st)) != NR_OK)
+      return r;
+  } else {
+    NR_CHECK_CUDA(cudaMemcpyAsync(s->d_G, s->h_G, sizeof(float) * 12 * s->K, cudaMemcpyHostToDevice, st));
+  }
   if (s->occ_source == kOccEllipsoids) {
     const int g = (int)s->occ_grid;
     const long n = (long)g * g * g;
@@ -703,10 +728,7 @@ extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *ro
     count_launches(1);
   }
   s->occ_dirty = true;   // a canonical-grid source is posed lazily, after the bias fold
-  // h_G / h_omega are reused by the next call: the copies must have read them
-  NR_CHECK_CUDA(cudaStreamSynchronize(st));
-  s->pose_set = true;
-  s->bias_dirty = true;
+  s->pose_dirty = false;
   return NR_OK;
 }
 
@@ -716,7 +738,10 @@ extern "C" nr_status nr_pose_transforms(nr_subject *s, float *G_out) {
     set_error("nr_pose_transforms: no pose set");
     return NR_ESTATE;
   }
-  memcpy(G_out, s->h_G, sizeof(float) * 12 * s->K);
+  NR_CHECK_CUDA(cudaSetDevice(s->device));
+  nr_status r = ensure_pose(s, nullptr);
+  if (r != NR_OK) return r;
+  NR_CHECK_CUDA(cudaMemcpy(G_out, s->d_G, sizeof(float) * 12 * s->K, cudaMemcpyDeviceToHost));
   return NR_OK;
 }
 
@@ -729,6 +754,7 @@ extern "C" nr_status nr_occupancy(nr_subject *s, uint32_t *bits_out) {
   NR_CHECK_CUDA(cudaSetDevice(s->device));
   nr_status r;
   if ((r = prepare_params(s, nullptr)) != NR_OK) return r;
+  if ((r = ensure_pose(s, nullptr)) != NR_OK) return r;
   if ((r = ensure_bias(s, nullptr)) != NR_OK) return r;
   if ((r = ensure_occupancy(s, nullptr)) != NR_OK) return r;
   const size_t words = (size_t)s->occ_grid * s->occ_grid * s->occ_grid / 32;
@@ -807,6 +833,7 @@ extern "C" nr_status nr_param(nr_subject *s, uint32_t which, float **dev, float 
     case NR_PARAM_HASH: p = s->table; g = s->g_table; n = s->n_table; break;
     case NR_PARAM_MLP: p = s->mlp; g = s->g_mlp; n = s->n_mlp; break;
     case NR_PARAM_RES: p = s->res; g = s->g_res; n = s->n_res; break;
+    case NR_PARAM_REFINER: p = s->ref; g = s->g_ref; n = s->n_ref; break;
     default: set_error("nr_param: unknown group %u", which); return NR_EINVAL;
   }
   if (dev) *dev = p;
@@ -819,6 +846,7 @@ extern "C" nr_status nr_params_changed(nr_subject *s) {
   NR_REQUIRE(subject_ok(s), "nr_params_changed: invalid handle");
   s->params_dirty = true;
   s->bias_dirty = true;
+  if (s->ref_layers) s->pose_dirty = s->pose_set;
   return NR_OK;
 }
 
@@ -854,9 +882,11 @@ extern "C" nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float
     if (s->f_bias1) cudaFree(s->f_bias1);
     if (s->f_dbias1) cudaFree(s->f_dbias1);
     if (s->f_cam) cudaFree(s->f_cam);
-    s->f_G = s->f_omega = s->f_bias1 = s->f_dbias1 = nullptr;
+    if (s->f_root) cudaFree(s->f_root);
+    s->f_G = s->f_omega = s->f_bias1 = s->f_dbias1 = s->f_root = nullptr;
     s->f_cam = nullptr;
     s->n_frames = s->frames_cap = 0;
+    NR_CHECK_CUDA(cudaMalloc(&s->f_root, (size_t)n_frames * 3 * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_G, G.size() * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_omega, om.size() * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_bias1, (size_t)n_frames * kWidth * 4));
@@ -867,7 +897,12 @@ extern "C" nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float
   NR_CHECK_CUDA(cudaMemcpyAsync(s->f_G, G.data(), G.size() * 4, cudaMemcpyHostToDevice, st));
   NR_CHECK_CUDA(cudaMemcpyAsync(s->f_omega, om.data(), om.size() * 4, cudaMemcpyHostToDevice, st));
   NR_CHECK_CUDA(cudaMemcpyAsync(s->f_cam, fr.data(), fr.size() * sizeof(Frame), cudaMemcpyHostToDevice, st));
+  std::vector<float> rt((size_t)n_frames * 3, 0.f);
+  if (root_t) memcpy(rt.data(), root_t, rt.size() * 4);
+  NR_CHECK_CUDA(cudaMemcpyAsync(s->f_root, rt.data(), rt.size() * 4, cudaMemcpyHostToDevice, st));
   NR_CHECK_CUDA(cudaStreamSynchronize(st));
+  s->h_fG = G;
+  s->fG_refined = false;
   s->n_frames = n_frames;
   return NR_OK;
 }

@@ -36,6 +36,8 @@ struct Rows {
   int dr5;     // residual output delta    4
   int denc;    // dL/d encoding            32
   int dgam;    // dL/d gamma               48
+  int dp;      // dL/d p_i per bone (pose refiner)  3 x 24
+  int xs;      // the sample position               3
   int total;
 };
 
@@ -51,6 +53,8 @@ static Rows make_rows(int H) {
   r.dr5 = o; o += 4;
   r.denc = o; o += kMlpIn;
   r.dgam = o; o += kResGammaPad;
+  r.dp = o; o += 3 * kBones;
+  r.xs = o; o += 3;
   r.total = o;
   return r;
 }
@@ -74,6 +78,8 @@ struct TrainDev {
   int acc_floats;         // floats per block accumulator
   int n_frames;
   Rows rw;
+  float *dG;              // [F][24][12] dL/dG of every frame (pose refiner), or NULL
+  int dG_smem;            // 1: the block sums dG in shared memory first
 };
 
 // ----------------------------------------------------------------- rays
@@ -296,15 +302,18 @@ __device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, 
 __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P, TrainDev T) {
   extern __shared__ float4 smem4[];
   float *sW = reinterpret_cast<float *>(smem4);
+  float *sdG = sW + P.lay.total;                       // [F][24][12] when T.dG_smem
   for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
     reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
+  if (T.dG && T.dG_smem)
+    for (int i = threadIdx.x; i < T.n_frames * kBones * 12; i += blockDim.x) sdG[i] = 0.f;
   __syncthreads();
   const BlobLayout &Ly = P.lay;
   const int stride = blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Rows &RW = T.rw;
   const int R_GAM = RW.gam, R_RH = RW.rh, R_ENC = RW.enc, R_CH = RW.ch, D_C = RW.dc, D_R = RW.dr, D_R5 = RW.dr5,
-            R_DENC = RW.denc, R_DGAM = RW.dgam, kRows = RW.total;
+            R_DENC = RW.denc, R_DGAM = RW.dgam, R_DP = RW.dp, R_XS = RW.xs, kRows = RW.total;
   float *colbase = T.scratch + (size_t)blockIdx.x * kRows * stride;
   float *col = colbase + threadIdx.x;                  // this thread's column
   const float *wcol = colbase + warp * 32;             // the warp's column 0
@@ -474,20 +483,37 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           ds2 += dh[2] * P.box_ih[2];
         }
         // ---------------- inverse-LBS backward: scatter into the weight volume
+        // and, for the pose refiner, dL/dp_i of each candidate p_i = G_i x:
+        //   x_skel = sum_i w_i p_i / D,  w_i = W_i(p_i)
+        //   dL/dp_i = (w_i / D) dL/dx_skel + dL/dw_i grad W_i(p_i)
         {
           const float D = fmaxf(S, kEpsW);
           const float m = S > kEpsW ? 1.f : 0.f;
           const int R = P.wres, R3 = R * R * R;
+          const size_t QC = quad_channel(R);
+          if (T.dG) {
+            col[(R_XS + 0) * stride] = s.x;
+            col[(R_XS + 1) * stride] = s.y;
+            col[(R_XS + 2) * stride] = s.z;
+          }
           for (int i = 0; i < kBones; ++i) {
             const float *g = G + 12 * i;
             const float p0 = fmaf(g[0], s.x, fmaf(g[1], s.y, fmaf(g[2], s.z, g[3])));
             const float p1 = fmaf(g[4], s.x, fmaf(g[5], s.y, fmaf(g[6], s.z, g[7])));
             const float p2 = fmaf(g[8], s.x, fmaf(g[9], s.y, fmaf(g[10], s.z, g[11])));
             const float dw = (ds0 * (p0 - m * xs0) + ds1 * (p1 - m * xs1) + ds2 * (p2 - m * xs2)) / D + dS_alpha;
-            if (dw == 0.f) continue;
             const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
             const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
             const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
+            if (T.dG) {
+              float gx, gy, gz;
+              const float w = trilinear_quad_grad(P.wquad + (size_t)i * QC, R, ux, uy, uz, gx, gy, gz);
+              const float a = w / D;
+              col[(R_DP + 3 * i + 0) * stride] = fmaf(a, ds0, dw * gx * P.vol_scale[0]);
+              col[(R_DP + 3 * i + 1) * stride] = fmaf(a, ds1, dw * gy * P.vol_scale[1]);
+              col[(R_DP + 3 * i + 2) * stride] = fmaf(a, ds2, dw * gz * P.vol_scale[2]);
+            }
+            if (dw == 0.f) continue;
             const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
             const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
             if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) continue;
@@ -547,7 +573,36 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         atomicAdd(accF + cur * kWidth + lane + 32, s1);
       }
     }
+    if (T.dG) {
+      // dL/dG_i of each frame: dR_i += dp_i x^T, dt_i += dp_i over the warp's 32 samples;
+      // lane owns 9 of the 24 x 12 entries and sums them per run of equal frames
+      const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
+      const int fl = j0 + lane < n ? (int)T.frame_id[(j0 + lane) / T.S] : -1;
+      for (int o = lane; o < kBones * 12; o += 32) {
+        const int i = o / 12, rr = (o % 12) >> 2, c = o & 3;
+        const float *dpr = wcol + (R_DP + 3 * i + rr) * stride;
+        const float *xr = wcol + (R_XS + (c < 3 ? c : 0)) * stride;
+        int cur = -1;
+        float v = 0.f;
+        for (int sI = 0; sI < 32; ++sI) {
+          const int fr = __shfl_sync(0xffffffffu, fl, sI);
+          if (fr < 0) break;
+          if (fr != cur) {
+            if (cur >= 0 && v != 0.f) atomicAdd((T.dG_smem ? sdG : T.dG) + cur * kBones * 12 + o, v);
+            cur = fr;
+            v = 0.f;
+          }
+          v = fmaf(dpr[sI], c < 3 ? xr[sI] : 1.f, v);
+        }
+        if (cur >= 0 && v != 0.f) atomicAdd((T.dG_smem ? sdG : T.dG) + cur * kBones * 12 + o, v);
+      }
+    }
     __syncwarp();
+  }
+  if (T.dG && T.dG_smem) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < T.n_frames * kBones * 12; i += blockDim.x)
+      if (sdG[i] != 0.f) atomicAdd(T.dG + i, sdG[i]);
   }
 }
 
@@ -665,7 +720,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
              "nr_train_step: bad Adam hyper-parameters");
   for (int k = 0; k < 4; ++k) NR_REQUIRE(b->lr_scale[k] >= 0.f, "nr_train_step: negative lr_scale");
-  NR_REQUIRE(b->loss_weight >= 0.f, "nr_train_step: negative loss_weight");
+  NR_REQUIRE(b->loss_weight >= 0.f && b->lr_scale_refiner >= 0.f, "nr_train_step: negative loss_weight or lr scale");
   if (s->n_frames == 0) {
     set_error("nr_train_step: call nr_set_frames first");
     return NR_ESTATE;
@@ -675,6 +730,17 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   nr_status r;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
   if ((r = fold_frame_biases(s, st)) != NR_OK) return r;
+  const bool refine = s->ref_layers != 0;
+  int launched = 0;
+  if (refine) {   // every frame's G from its refined pose (Sec. 4.1)
+    if ((r = launch_refine_fk(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_G, st)) != NR_OK)
+      return r;
+    s->fG_refined = true;
+  } else if (s->fG_refined) {   // the refiner was switched off: back to the estimated poses
+    NR_CHECK_CUDA(cudaMemcpyAsync(s->f_G, s->h_fG.data(), s->h_fG.size() * 4, cudaMemcpyHostToDevice, st));
+    NR_CHECK_CUDA(cudaStreamSynchronize(st));
+    s->fG_refined = false;
+  }
   nr_render_opts o{};
   o.mlp_dtype = NR_F32;
   o.feat_dtype = NR_F32;
@@ -716,6 +782,13 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_CHECK_CUDA(cudaMemsetAsync(s->g_table, 0, s->n_table * 4, st));
   NR_CHECK_CUDA(cudaMemsetAsync(s->t_wacc, 0, n_acc * A * 4, st));
   NR_CHECK_CUDA(cudaMemsetAsync(s->loss_acc, 0, sizeof(float), st));
+  const size_t n_dG = (size_t)s->n_frames * kBones * 12;
+  const bool dG_smem = refine && s->n_frames <= 16;
+  if (refine) {
+    if ((r = grow(s->f_dG, s->f_dG_cap, n_dG)) != NR_OK) return r;
+    NR_CHECK_CUDA(cudaMemsetAsync(s->f_dG, 0, n_dG * 4, st));
+    NR_CHECK_CUDA(cudaMemsetAsync(s->g_ref, 0, s->n_ref * 4, st));
+  }
 
   TrainDev T{};
   T.frame_id = b->frame_id;
@@ -743,6 +816,8 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.acc_floats = A;
   T.n_frames = (int)s->n_frames;
   T.rw = rows;
+  T.dG = refine ? s->f_dG : nullptr;
+  T.dG_smem = dG_smem ? 1 : 0;
 
   train_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
                                                                      s->bmax[1], s->bmax[2]);
@@ -753,7 +828,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_CHECK_CUDA(cudaGetLastError());
   train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
   NR_CHECK_CUDA(cudaGetLastError());
-  const size_t smem_b = sizeof(float) * s->lay.total;
+  const size_t smem_b = sizeof(float) * (s->lay.total + (dG_smem ? n_dG : 0));
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);
   NR_CHECK_CUDA(cudaGetLastError());
@@ -773,7 +848,10 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   }
   scatter_mlp_kernel<<<(sa.m.n_mlp + 255) / 256, 256, 0, st>>>(s->t_red, sa, s->g_mlp);
   NR_CHECK_CUDA(cudaGetLastError());
-  int launched = 7;
+  launched += 7;
+  if (refine && (r = launch_refine_bwd(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_dG, s->g_ref,
+                                       st)) != NR_OK)
+    return r;
   if (!(b->flags & NR_GRAD_ONLY)) {
     const uint32_t mask = b->train_mask ? b->train_mask : NR_TRAIN_ALL;
     s->adam_t += 1;
@@ -795,6 +873,17 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
       adam_kernel<<<nb, 256, 0, st>>>(g.p, g.g, s->adam_m + g.off, s->adam_v + g.off, g.n, lr, b->beta1, b->beta2,
                                       b->eps, (float)c1, (float)c2);
       ++launched;
+    }
+    if (refine && (mask & NR_TRAIN_REFINER)) {
+      s->ref_t += 1;
+      const double r1 = 1.0 / (1.0 - pow((double)b->beta1, (double)s->ref_t));
+      const double r2 = 1.0 / (1.0 - pow((double)b->beta2, (double)s->ref_t));
+      const float lr = b->lr * (b->lr_scale_refiner > 0.f ? b->lr_scale_refiner : 1.f);
+      const int nb = (int)std::min<size_t>((s->n_ref + 255) / 256, (size_t)blocks * 8);
+      adam_kernel<<<nb, 256, 0, st>>>(s->ref, s->g_ref, s->ref_m, s->ref_v, s->n_ref, lr, b->beta1, b->beta2, b->eps,
+                                      (float)r1, (float)r2);
+      ++launched;
+      s->pose_dirty = s->pose_set;   // the current pose's refinement moved
     }
     NR_CHECK_CUDA(cudaGetLastError());
     s->params_dirty = true;

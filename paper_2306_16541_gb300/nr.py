@@ -22,8 +22,8 @@ NR_F32, NR_F16, NR_BF16, NR_FP8E4M3 = range(4)
 DTYPES = {"f32": NR_F32, "f16": NR_F16, "bf16": NR_BF16, "fp8": NR_FP8E4M3}
 NR_POSE_MATRICES = 1
 NR_GRAD_ONLY = 1
-NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_ALL = 1, 2, 4, 8, 15
-NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES = range(4)
+NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_REFINER, NR_TRAIN_ALL = 1, 2, 4, 8, 16, 31
+NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES, NR_PARAM_REFINER = range(5)
 # Per-group learning-rate multipliers (weight volume, hash, canonical MLP, residual MLP):
 # Sec. 5.2 uses a 10x smaller rate for the networks other than the NeRF network.
 PAPER_LR_SCALE = (0.1, 1.0, 1.0, 0.1)
@@ -69,7 +69,8 @@ class nr_train_batch(C.Structure):
                 ("target_rgb", _fp), ("n_samples", C.c_uint32), ("bg", C.c_float * 3),
                 ("step_seed", C.c_uint64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("hann_alpha", C.c_float), ("flags", C.c_uint32),
-                ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4), ("loss_weight", C.c_float)]
+                ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4), ("loss_weight", C.c_float),
+                ("lr_scale_refiner", C.c_float)]
 
 
 class nr_request(C.Structure):
@@ -104,6 +105,7 @@ def _load() -> C.CDLL:
         "nr_refresh_occupancy": ([vp, C.c_float, C.c_uint32, C.c_float, vp], C.c_int),
         "nr_set_canonical_occupancy": ([vp, _up, C.c_float, vp], C.c_int),
         "nr_canonical_occupancy": ([vp, _up], C.c_int),
+        "nr_set_pose_refiner": ([vp, C.c_uint32, C.c_uint32, _fp, vp], C.c_int),
         "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
@@ -314,6 +316,19 @@ def nr_canonical_occupancy(h, grid: int = 128) -> np.ndarray:
     return bits
 
 
+def nr_set_pose_refiner(h, layers, stream=None) -> None:
+    """layers: MLP_theta as [(W [out][in], b [out]), ...] (hidden layers then the output
+    layer), or None to switch the refiner off."""
+    if layers is None:
+        check(lib.nr_set_pose_refiner(h, 0, 0, None, _stream(stream)), "nr_set_pose_refiner")
+        return
+    width = int(layers[0][0].shape[0])
+    flat = np.ascontiguousarray(np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(),
+                                                                np.asarray(b, np.float32).ravel()])
+                                                for W, b in layers]), np.float32)
+    check(lib.nr_set_pose_refiner(h, width, len(layers) - 1, _ptr(flat), _stream(stream)), "nr_set_pose_refiner")
+
+
 class Subject:
     """One performer resident on the GPU (owns an nr_subject handle)."""
 
@@ -344,7 +359,7 @@ class Subject:
     def train_step(self, frame_id, px, py, target_rgb, n_samples: int, step_seed: int, lr: float = 1e-2,
                    betas=(0.9, 0.99), eps: float = 1e-8, bg=(0.0, 0.0, 0.0), hann_alpha: float = -1.0,
                    grad_only: bool = False, train_mask: int = 0, lr_scale=(0.0, 0.0, 0.0, 0.0),
-                   loss_weight: float = 0.0, stream=None) -> float:
+                   loss_weight: float = 0.0, lr_scale_refiner: float = 0.0, stream=None) -> float:
         b = nr_train_batch()
         b.n_rays = int(frame_id.shape[0])
         b.frame_id = C.cast(C.c_void_p(frame_id.data_ptr()), _up)
@@ -357,6 +372,7 @@ class Subject:
         b.hann_alpha, b.flags, b.train_mask = float(hann_alpha), NR_GRAD_ONLY if grad_only else 0, int(train_mask)
         b.lr_scale[:] = [float(v) for v in lr_scale]
         b.loss_weight = float(loss_weight)
+        b.lr_scale_refiner = float(lr_scale_refiner)
         return nr_train_step(self.h, b, stream)
 
     def param(self, which: int):
@@ -379,6 +395,9 @@ class Subject:
 
     def set_canonical_occupancy(self, bits, s_min: float = OCC_S_MIN, stream=None):
         nr_set_canonical_occupancy(self.h, bits, s_min, stream)
+
+    def set_pose_refiner(self, layers, stream=None):
+        nr_set_pose_refiner(self.h, layers, stream)
 
     def canonical_occupancy(self):
         return nr_canonical_occupancy(self.h, self.occ_grid)

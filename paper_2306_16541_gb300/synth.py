@@ -347,6 +347,19 @@ def subject(seed: int, *, vol_res: int = 32, hash_levels: int = 8, log2_t: int =
     return d
 
 
+def refiner_dims(width: int = 256, hidden_layers: int = 4) -> list[tuple[int, int]]:
+    """(in, out) of each pose-refiner layer: 3(K-1) joint angles -> width x hidden -> 3(K-1)."""
+    n = 3 * (N_BONES - 1)
+    return [(n, width)] + [(width, width)] * (hidden_layers - 1) + [(width, n)]
+
+
+def refiner_layers(seed: int, width: int = 256, hidden_layers: int = 4, last_std: float = 1e-5):
+    """Seeded MLP_theta weights: Kaiming hidden layers, a near-zero output layer (the
+    refined pose starts at the estimate)."""
+    rng = np.random.default_rng(seed)
+    return kaiming_layers(rng, refiner_dims(width, hidden_layers), last_std=last_std)
+
+
 def shaped_density(subj: dict, beta: float = 8.0, bias: float = -4.0, keep_ellipsoids: bool = False) -> dict:
     """A copy of `subj` (made with ellipsoids) whose canonical density follows the performer's body.
 
