@@ -140,13 +140,31 @@ nr_status nr_set_pose(nr_subject *s, const float *axis_angle, const float *root_
  * per layer, W[out][in] row-major then b[out] (69 -> width, width -> width,
  * ..., width -> 69).  The refined local rotation of joint j >= 1 is
  * Rot(Delta_omega_j) Rot(omega_j); the root keeps its estimate; the residual
- * MLP stays conditioned on the estimated angles.  Training (nr_train_step)
- * then back-propagates dL/dG_i of every frame, reduced over the batch's
- * samples, through the kinematic chain into MLP_theta (Adam group
- * NR_TRAIN_REFINER, parameters NR_PARAM_REFINER).  params == NULL switches
+ * MLP is conditioned on the updated angles Omega^o, omega^o_j = Log of the
+ * refined local rotation (angles below pi).  Training (nr_train_step) then
+ * back-propagates dL/dG_i of every frame, reduced over the batch's samples,
+ * through the kinematic chain, and dL/dOmega^o through the rotation log,
+ * into MLP_theta (Adam group NR_TRAIN_REFINER, parameters NR_PARAM_REFINER).  params == NULL switches
  * the refiner off.  The Adam moments restart at each call. */
 nr_status nr_set_pose_refiner(nr_subject *s, uint32_t width, uint32_t hidden_layers, const float *params,
                               void *stream);
+
+/* Weight-volume generator CNN_skel (Sec. 4.2): W^c = CNN_skel(z) replaces the
+ * stored weight volume.  A fully-connected layer maps the constant latent
+ * z[256] to channels[0] values (a channels[0] x 1^3 tensor); five transposed
+ * convolutions (kernel 4, stride 2, padding 1) take it to 32^3 with channels
+ * channels[1..4] and then 25; LeakyReLU(0.2) follows the fully-connected layer
+ * and every transposed convolution but the last; the 25 channels pass through
+ * a softmax over channels after adding log_prior [25][32][32][32] (may be
+ * NULL).  params (host) packs W_fc [channels[0]][256], b_fc, then per
+ * convolution W [C_in][C_out][4][4][4], b [C_out].  Requires wvol_res == 32.
+ * The volume is regenerated whenever the generator's parameters change;
+ * training (nr_train_step) back-propagates dL/dW^c through it (Adam group
+ * NR_TRAIN_CNN, parameters NR_PARAM_CNN) and no longer updates the volume
+ * directly.  params == NULL switches the generator off (the volume keeps its
+ * last generated values).  Host pointers, copied; the Adam moments restart. */
+nr_status nr_set_weight_cnn(nr_subject *s, const uint32_t *channels, const float *params, const float *z,
+                            const float *log_prior, void *stream);
 
 /* Pinhole camera, OpenCV convention (x right, y down, z forward).
  * Pixel (u, v) looks along R^T ((u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1)
@@ -227,7 +245,8 @@ nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float *axis_angl
 #define NR_TRAIN_MLP 4u
 #define NR_TRAIN_RES 8u
 #define NR_TRAIN_REFINER 16u
-#define NR_TRAIN_ALL 31u
+#define NR_TRAIN_CNN 32u
+#define NR_TRAIN_ALL 63u
 
 /* One training batch of pixel rays.  frame_id, px, py: device uint32[n];
  * target_rgb: device float32[n][3].  Samples are stratified: bin i of the
@@ -251,6 +270,7 @@ typedef struct {
   float loss_weight;             /* lambda_mse: L = lambda_mse * MSE (Sec. 5.2 uses 0.2 beside
                                     LPIPS); 0 means 1 */
   float lr_scale_refiner;        /* lr multiplier of the pose refiner; 0 means 1 */
+  float lr_scale_cnn;            /* lr multiplier of the weight-volume generator; 0 means 1 */
 } nr_train_batch;
 
 /* Forward, loss L = loss_weight * mean over rays and channels of (C^ - C_gt)^2, the
@@ -265,6 +285,7 @@ nr_status nr_train_step(nr_subject *s, const nr_train_batch *batch, float *loss_
 #define NR_PARAM_MLP 2u     /* canonical MLP, packed as in the descriptor */
 #define NR_PARAM_RES 3u     /* residual MLP, packed as in the descriptor */
 #define NR_PARAM_REFINER 4u /* pose refiner MLP_theta, packed as in nr_set_pose_refiner */
+#define NR_PARAM_CNN 5u     /* weight-volume generator CNN_skel, packed as in nr_set_weight_cnn */
 /* Device pointers of a parameter group (float32) and of its gradient buffer,
  * and its element count.  Writing the parameters through *dev_ptr is allowed
  * between calls; call nr_params_changed() afterwards. */

@@ -88,11 +88,10 @@ def sample_alpha(out, delta, live):
 
 def pose_inputs(subj: dict, axis_angle, root_t, refiner=None):
     """FP64 G (R [K,3,3], t [K,3]) and the flattened joint angles Omega [3K] that condition
-    MLP_res; with `refiner` (MLP_theta layers, Sec. 4.1) G is that of the refined pose."""
+    MLP_res; with `refiner` (MLP_theta layers, Sec. 4.1) both are those of the refined pose."""
     omega = t64(np.asarray(axis_angle, np.float32)).reshape(-1)
     if refiner is not None:
-        R, t = refine.refined_transforms(subj["parents"], subj["rest_joints"], axis_angle, root_t, refiner)
-        return R, t, omega
+        return refine.refined_pose(subj["parents"], subj["rest_joints"], axis_angle, root_t, refiner)
     R, t = fk.bone_transforms(subj["parents"], subj["rest_joints"], axis_angle, root_t)
     return torch.from_numpy(R), torch.from_numpy(t), omega
 

@@ -159,7 +159,7 @@ struct nr_subject {
   float h_omega[24 * 3];
   float h_root[3] = {0.f, 0.f, 0.f};
   float *d_G = nullptr;              // [24][12]
-  float *d_omega = nullptr;          // [72] joint angles, then [3] root translation
+  float *d_omega = nullptr;          // [72] joint angles, [3] root translation, [72] refined angles
   float *d_bias1 = nullptr;          // [64]
   bool bias_dirty = true;
   float *ellip = nullptr;            // [24][15]
@@ -173,11 +173,19 @@ struct nr_subject {
   float *ref = nullptr, *g_ref = nullptr, *ref_m = nullptr, *ref_v = nullptr;
   size_t n_ref = 0;
   uint32_t ref_t = 0;                // Adam steps of the refiner
+  // CNN_skel weight-volume generator (Sec. 4.2); cnn_on: wvol = CNN(z)
+  bool cnn_on = false, cnn_dirty = false;
+  uint32_t cnn_ch[5] = {0, 0, 0, 0, 0};
+  float *cnn = nullptr, *g_cnn = nullptr, *cnn_m = nullptr, *cnn_v = nullptr;
+  float *cnn_z = nullptr, *cnn_prior = nullptr, *cnn_act = nullptr, *cnn_grad = nullptr;
+  size_t n_cnn = 0;
+  uint32_t cnn_t = 0;                // Adam steps of the generator
   // training frames
   uint32_t n_frames = 0, frames_cap = 0;
   std::vector<float> h_fG;           // host forward kinematics of the estimated frame poses
   bool fG_refined = false;           // f_G holds refined poses
   float *f_root = nullptr;           // [F][3]
+  float *f_omega_o = nullptr;        // [F][72] refined joint angles (refiner)
   float *f_dG = nullptr;             // [F][24][12] dL/dG (refiner)
   size_t f_dG_cap = 0;
   float *f_G = nullptr;              // [F][24][12]
@@ -233,10 +241,13 @@ nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const f
 nr_status ensure_occupancy(nr_subject *s, cudaStream_t st);    // posed grid of the current pose (kOccGrid)
 nr_status ensure_pose(nr_subject *s, cudaStream_t st);         // d_G (refined if MLP_theta is on), bitfields
 nr_status launch_refine_fk(const nr_subject *s, const float *omega, int omega_stride, const float *root,
-                           int root_stride, int n, float *G, cudaStream_t st);
+                           int root_stride, int n, float *G, float *omega_o, int omega_o_stride, cudaStream_t st);
 nr_status launch_refine_bwd(const nr_subject *s, const float *omega, int omega_stride, const float *root,
-                            int root_stride, int n, const float *dG, float *g, cudaStream_t st);
+                            int root_stride, int n, const float *dG, const float *dbias, float *g, cudaStream_t st);
+const float *pose_omega(const nr_subject *s);   // angles conditioning MLP_res for the current pose (device)
 size_t refiner_param_count(uint32_t width, uint32_t layers);
+nr_status cnn_forward(nr_subject *s, cudaStream_t st);         // wvol = CNN_skel(z)
+nr_status cnn_backward(nr_subject *s, cudaStream_t st);        // g_cnn from g_wvol
 nr_status launch_occupancy_field(const FieldParams &P, int mode, uint32_t *bits, int device, cudaStream_t st);
 nr_status launch_fold_bias(const nr_subject *s, const float *omega_dev, float *bias_dev, int n_poses, cudaStream_t st);
 bool subject_ok(const nr_subject *s);

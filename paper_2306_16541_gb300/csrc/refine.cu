@@ -103,6 +103,61 @@ __device__ void rodrigues_grad(const double *v, const double *dR, double *dv) {
   }
 }
 
+// Log of a rotation (angle in [0, pi)): a = (R_32 - R_23, R_13 - R_31, R_21 - R_12) / 2 =
+// sin(th) n, cos(th) = (tr R - 1) / 2, v = th / sin(th) a (1 + th^2 / 6 below sin = 1e-8).
+__device__ void rot_log(const double *R, double *v) {
+  const double a0 = 0.5 * (R[7] - R[5]), a1 = 0.5 * (R[2] - R[6]), a2 = 0.5 * (R[3] - R[1]);
+  const double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
+  const double s = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+  const double th = atan2(s, c);
+  const double k = s < 1e-8 ? 1.0 + th * th / 6.0 : th / s;
+  v[0] = k * a0;
+  v[1] = k * a1;
+  v[2] = k * a2;
+}
+
+// y = M^T x for M = I + p K + q K^2, K = [v]_x:  y_r = x_r + sum_c (p K_cr + q (K^2)_cr) x_c.
+__device__ __forceinline__ void so3_poly_t(const double *v, double p, double q, const double *x, double *y) {
+  double K[9], K2[9];
+  skew(v, K);
+  mat3_mul(K, K, K2);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double a = x[r];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a += (p * K[3 * c + r] + q * K2[3 * c + r]) * x[c];
+    y[r] = a;
+  }
+}
+
+// Derivative of phi = Log(Rot(d) R0) in d: dphi = J_l^{-1}(phi) J_l(d) dd, with the left
+// Jacobian J_l(v) = I + (1 - cos th)/th^2 K + (th - sin th)/th^3 K^2 and its inverse
+// J_l^{-1}(phi) = I - K/2 + (1/th^2 - (1 + cos th) / (2 th sin th)) K^2.  Returns dd += J_l(d)^T
+// J_l^{-1}(phi)^T g.
+__device__ void log_compose_grad(const double *d, const double *phi, const double *g, double *dd) {
+  double t2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], q;
+  if (t2 < 1e-6) {
+    q = 1.0 / 12.0 + t2 / 720.0;
+  } else {
+    const double t = sqrt(t2);
+    q = 1.0 / t2 - (1.0 + cos(t)) / (2.0 * t * sin(t));
+  }
+  double y[3], z[3];
+  so3_poly_t(phi, -0.5, q, g, y);
+  t2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double p1, q1;
+  if (t2 < 1e-6) {
+    p1 = 0.5 - t2 / 24.0;
+    q1 = 1.0 / 6.0 - t2 / 120.0;
+  } else {
+    const double t = sqrt(t2);
+    p1 = (1.0 - cos(t)) / t2;
+    q1 = (t - sin(t)) / (t2 * t);
+  }
+  so3_poly_t(d, p1, q1, y, z);
+  for (int a = 0; a < 3; ++a) dd[a] += z[a];
+}
+
 // Shared state of one pose's forward pass.
 struct RefShared {
   float in[kRefIn + 3];
@@ -173,13 +228,30 @@ __device__ void refine_forward(const RefParams &P, const float *om, const float 
   __syncthreads();
 }
 
-// G_i = (R_i | t_i), R_i = AR_i^T, t_i = J_i - AR_i^T At_i, rows [R | t] in float32.
+// G_i = (R_i | t_i), R_i = AR_i^T, t_i = J_i - AR_i^T At_i, rows [R | t] in float32, and the
+// updated joint angles Omega^o (root: omega_0; j >= 1: Log of the refined local rotation).
 __global__ void __launch_bounds__(kRefThreads) refine_fk_kernel(RefParams P, const float *__restrict__ omega,
                                                                 int omega_stride, const float *__restrict__ root,
-                                                                int root_stride, float *__restrict__ G) {
+                                                                int root_stride, float *__restrict__ G,
+                                                                float *__restrict__ omega_o, int omega_o_stride) {
   __shared__ RefShared sh;
   const int f = blockIdx.x, t = threadIdx.x;
-  refine_forward(P, omega + (size_t)f * omega_stride, root + (size_t)f * root_stride, sh);
+  const float *om = omega + (size_t)f * omega_stride;
+  refine_forward(P, om, root + (size_t)f * root_stride, sh);
+  if (omega_o && t < kBones) {
+    float *oo = omega_o + (size_t)f * omega_o_stride + 3 * t;
+    if (t == 0) {
+      oo[0] = om[0];
+      oo[1] = om[1];
+      oo[2] = om[2];
+    } else {
+      double v[3];
+      rot_log(sh.Rl[t], v);
+      oo[0] = (float)v[0];
+      oo[1] = (float)v[1];
+      oo[2] = (float)v[2];
+    }
+  }
   if (t < kBones) {
     float *g = G + ((size_t)f * kBones + t) * 12;
     for (int r = 0; r < 3; ++r) {
@@ -195,20 +267,35 @@ __global__ void __launch_bounds__(kRefThreads) refine_fk_kernel(RefParams P, con
 }
 
 // From dL/dG [F][24][12] of each pose to dL/d theta (added into g with atomics).
+// dbias: [F][64] dL/d(first residual bias of each frame), W1: residual layer 1, rows of
+// w1_stride floats whose columns w1_col.. hold W_Omega (bias1 = b1 + W_Omega Omega^o); NULL
+// when the residual MLP is off.
 __global__ void __launch_bounds__(kRefThreads) refine_bwd_kernel(RefParams P, const float *__restrict__ omega,
                                                                  int omega_stride, const float *__restrict__ root,
                                                                  int root_stride, const float *__restrict__ dG,
-                                                                 float *__restrict__ g) {
+                                                                 const float *__restrict__ dbias,
+                                                                 const float *__restrict__ W1, int w1_stride,
+                                                                 int w1_col, float *__restrict__ g) {
   __shared__ RefShared sh;
   __shared__ double dAR[kBones][9], dAt[kBones][3], dRl[kBones][9];
-  __shared__ float dcur[kRefThreads], dnext[kRefThreads], dout[kRefIn + 3];
+  __shared__ float dcur[kRefThreads], dnext[kRefThreads], dout[kRefIn + 3], dom[3 * kBones];
   const int f = blockIdx.x, t = threadIdx.x;
   const float *gG = dG + (size_t)f * kBones * 12;
-  // frames the batch did not touch have dG = 0: nothing to do
+  const float *gb = dbias ? dbias + (size_t)f * kWidth : nullptr;
+  // frames the batch did not touch have dG = 0 and dbias = 0: nothing to do
   bool any = false;
   for (int e = t; e < kBones * 12; e += blockDim.x) any |= gG[e] != 0.f;
+  if (gb)
+    for (int e = t; e < kWidth; e += blockDim.x) any |= gb[e] != 0.f;
   if (!__syncthreads_or(any)) return;
   refine_forward(P, omega + (size_t)f * omega_stride, root + (size_t)f * root_stride, sh);
+  // dL/dOmega^o = W_Omega^T dL/dbias1
+  if (t < 3 * kBones) {
+    float a = 0.f;
+    if (gb)
+      for (int q = 0; q < kWidth; ++q) a = fmaf(W1[(size_t)q * w1_stride + w1_col + t], gb[q], a);
+    dom[t] = a;
+  }
   // G_i -> (AR_i, At_i):  R_i[r][c] = AR_i[c][r],  t_i[r] = J_i[r] - sum_c AR_i[c][r] At_i[c]
   if (t < kBones) {
     const float *d = gG + 12 * t;
@@ -261,6 +348,13 @@ __global__ void __launch_bounds__(kRefThreads) refine_bwd_kernel(RefParams P, co
     const double v[3] = {sh.delta[3 * (t - 1)], sh.delta[3 * (t - 1) + 1], sh.delta[3 * (t - 1) + 2]};
     double dv[3];
     rodrigues_grad(v, dRd, dv);
+    // omega^o_j = Log(Rot(Delta_j) Rot(omega_j)) feeds the residual MLP
+    const double go[3] = {dom[3 * t], dom[3 * t + 1], dom[3 * t + 2]};
+    if (go[0] != 0.0 || go[1] != 0.0 || go[2] != 0.0) {
+      double phi[3];
+      rot_log(sh.Rl[t], phi);
+      log_compose_grad(v, phi, go, dv);
+    }
     for (int a = 0; a < 3; ++a) dout[3 * (t - 1) + a] = (float)dv[a];
   }
   __syncthreads();
@@ -324,16 +418,20 @@ static RefParams ref_params(const nr_subject *s) {
 }
 
 nr_status launch_refine_fk(const nr_subject *s, const float *omega, int omega_stride, const float *root,
-                           int root_stride, int n, float *G, cudaStream_t st) {
-  refine_fk_kernel<<<n, kRefThreads, 0, st>>>(ref_params(s), omega, omega_stride, root, root_stride, G);
+                           int root_stride, int n, float *G, float *omega_o, int omega_o_stride, cudaStream_t st) {
+  refine_fk_kernel<<<n, kRefThreads, 0, st>>>(ref_params(s), omega, omega_stride, root, root_stride, G, omega_o,
+                                              omega_o_stride);
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
   return NR_OK;
 }
 
 nr_status launch_refine_bwd(const nr_subject *s, const float *omega, int omega_stride, const float *root,
-                            int root_stride, int n, const float *dG, float *g, cudaStream_t st) {
-  refine_bwd_kernel<<<n, kRefThreads, 0, st>>>(ref_params(s), omega, omega_stride, root, root_stride, dG, g);
+                            int root_stride, int n, const float *dG, const float *dbias, float *g, cudaStream_t st) {
+  const int gd = res_gamma_dims(s);
+  refine_bwd_kernel<<<n, kRefThreads, 0, st>>>(ref_params(s), omega, omega_stride, root, root_stride, dG,
+                                               s->res_enabled ? dbias : nullptr, s->res, gd + 3 * (int)s->K, gd,
+                                               g);
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
   return NR_OK;

@@ -120,7 +120,7 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
     return fail(e, "slot allocation " #p);
   if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
   SLOT_ALLOC(sl->d_G, kBones * 12 * sizeof(float));
-  SLOT_ALLOC(sl->d_omega, (kBones * 3 + 3) * sizeof(float));
+  SLOT_ALLOC(sl->d_omega, (2 * kBones * 3 + 3) * sizeof(float));
   SLOT_ALLOC(sl->d_bias1, kWidth * sizeof(float));
   SLOT_ALLOC(sl->bits, (size_t)grid * grid * grid / 8);
   SLOT_ALLOC(sl->w.samp, kSlotSamples * sizeof(float4));
@@ -171,14 +171,17 @@ static nr_status launch_request(nr_server *srv, Slot *sl, Request &q, DoneCtx *c
   NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_omega, sl->h_pose + kBones * 12, sizeof(float) * (kBones * 3 + 3),
                                 cudaMemcpyHostToDevice, st));
   nr_status rc;
-  if (s->ref_layers) {   // the refined pose (Sec. 4.1), on the device
-    if ((rc = launch_refine_fk(s, sl->d_omega, 3 * kBones, sl->d_omega + 3 * kBones, 3, 1, sl->d_G, st)) != NR_OK)
+  const float *omega_res = sl->d_omega;
+  if (s->ref_layers) {   // the refined pose and updated angles (Sec. 4.1), on the device
+    if ((rc = launch_refine_fk(s, sl->d_omega, 3 * kBones, sl->d_omega + 3 * kBones, 3, 1, sl->d_G,
+                               sl->d_omega + 3 * kBones + 3, 3 * kBones, st)) != NR_OK)
       return rc;
+    omega_res = sl->d_omega + 3 * kBones + 3;
   } else {
     forward_kinematics(s, r.axis_angle, r.root_t, sl->h_pose);
     NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_G, sl->h_pose, sizeof(float) * kBones * 12, cudaMemcpyHostToDevice, st));
   }
-  if ((rc = launch_fold_bias(s, sl->d_omega, sl->d_bias1, 1, st)) != NR_OK) return rc;
+  if ((rc = launch_fold_bias(s, omega_res, sl->d_bias1, 1, st)) != NR_OK) return rc;
   if (r.opts.use_occupancy && (rc = launch_posed_bitfield(s, sl->d_G, sl->d_bias1, sl->bits, st)) != NR_OK) return rc;
   FieldParams P = field_params(s, &r.opts);
   P.G = sl->d_G;

@@ -344,6 +344,12 @@ static int pack_tc_all(const nr_subject *s, const MasterOffsets &m, cudaStream_t
 }
 
 nr_status prepare_params(nr_subject *s, cudaStream_t st) {
+  if (s->cnn_on && s->cnn_dirty) {   // the weight volume is generated (Sec. 4.2)
+    nr_status r = cnn_forward(s, st);
+    if (r != NR_OK) return r;
+    s->cnn_dirty = false;
+    s->params_dirty = true;
+  }
   if (!s->params_dirty) return NR_OK;
   const MasterOffsets m = master_offsets(s);
   const BlobLayout &b = s->lay;
@@ -464,7 +470,7 @@ nr_status ensure_occupancy(nr_subject *s, cudaStream_t st) {
 
 nr_status ensure_bias(nr_subject *s, cudaStream_t st) {
   if (!s->bias_dirty) return NR_OK;
-  fold_pose_bias_kernel<<<1, kWidth, 0, st>>>(s->res, res_gamma_dims(s), 3 * (int)s->K, s->d_omega, s->d_bias1);
+  fold_pose_bias_kernel<<<1, kWidth, 0, st>>>(s->res, res_gamma_dims(s), 3 * (int)s->K, pose_omega(s), s->d_bias1);
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
   s->bias_dirty = false;
@@ -473,8 +479,8 @@ nr_status ensure_bias(nr_subject *s, cudaStream_t st) {
 
 nr_status fold_frame_biases(nr_subject *s, cudaStream_t st) {
   if (s->n_frames == 0) return NR_OK;
-  fold_pose_bias_kernel<<<s->n_frames, kWidth, 0, st>>>(s->res, res_gamma_dims(s), 3 * (int)s->K, s->f_omega,
-                                                         s->f_bias1);
+  fold_pose_bias_kernel<<<s->n_frames, kWidth, 0, st>>>(s->res, res_gamma_dims(s), 3 * (int)s->K,
+                                                         s->ref_layers ? s->f_omega_o : s->f_omega, s->f_bias1);
   NR_CHECK_CUDA(cudaGetLastError());
   return NR_OK;
 }
@@ -543,7 +549,8 @@ static void free_subject(nr_subject *s) {
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
                   s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
-                  s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG};
+                  s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG, s->f_omega_o,
+                  s->cnn, s->g_cnn, s->cnn_m, s->cnn_v, s->cnn_z, s->cnn_prior, s->cnn_act, s->cnn_grad};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
@@ -636,7 +643,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->tc_bf16, (size_t)s->tlay.total * 2);
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
   ALLOC(s->d_G, kBones * 12 * 4);
-  ALLOC(s->d_omega, (kBones * 3 + 3) * 4);
+  ALLOC(s->d_omega, (2 * kBones * 3 + 3) * 4);
   ALLOC(s->d_bias1, kWidth * 4);
   ALLOC(s->counter, 16 * 4);
   if (s->has_ellipsoids) {
@@ -661,7 +668,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
     H2D(s->ellip, d->ellipsoids, kBones * 15 * 4);
   }
 #undef H2D
-  e = cudaMemsetAsync(s->d_omega, 0, (kBones * 3 + 3) * 4, st);
+  e = cudaMemsetAsync(s->d_omega, 0, (2 * kBones * 3 + 3) * 4, st);
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync omega");
   // the call's host arrays may be freed on return: finish the copies first
   e = cudaStreamSynchronize(st);
@@ -714,7 +721,8 @@ nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
   if (!s->pose_dirty || !s->pose_set) return NR_OK;
   nr_status r;
   if (s->ref_layers && !s->pose_matrices) {
-    if ((r = launch_refine_fk(s, s->d_omega, 3 * kBones, s->d_omega + 3 * kBones, 3, 1, s->d_G, st)) != NR_OK)
+    if ((r = launch_refine_fk(s, s->d_omega, 3 * kBones, s->d_omega + 3 * kBones, 3, 1, s->d_G,
+                              s->d_omega + 3 * kBones + 3, 3 * kBones, st)) != NR_OK)
       return r;
   } else {
     NR_CHECK_CUDA(cudaMemcpyAsync(s->d_G, s->h_G, sizeof(float) * 12 * s->K, cudaMemcpyHostToDevice, st));
@@ -728,8 +736,13 @@ nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
     count_launches(1);
   }
   s->occ_dirty = true;   // a canonical-grid source is posed lazily, after the bias fold
+  s->bias_dirty = true;  // the refined angles condition MLP_res
   s->pose_dirty = false;
   return NR_OK;
+}
+
+const float *nr::pose_omega(const nr_subject *s) {
+  return (s->ref_layers && !s->pose_matrices) ? s->d_omega + 3 * kBones + 3 : s->d_omega;
 }
 
 extern "C" nr_status nr_pose_transforms(nr_subject *s, float *G_out) {
@@ -834,6 +847,7 @@ extern "C" nr_status nr_param(nr_subject *s, uint32_t which, float **dev, float 
     case NR_PARAM_MLP: p = s->mlp; g = s->g_mlp; n = s->n_mlp; break;
     case NR_PARAM_RES: p = s->res; g = s->g_res; n = s->n_res; break;
     case NR_PARAM_REFINER: p = s->ref; g = s->g_ref; n = s->n_ref; break;
+    case NR_PARAM_CNN: p = s->cnn; g = s->g_cnn; n = s->n_cnn; break;
     default: set_error("nr_param: unknown group %u", which); return NR_EINVAL;
   }
   if (dev) *dev = p;
@@ -847,6 +861,7 @@ extern "C" nr_status nr_params_changed(nr_subject *s) {
   s->params_dirty = true;
   s->bias_dirty = true;
   if (s->ref_layers) s->pose_dirty = s->pose_set;
+  if (s->cnn_on) s->cnn_dirty = true;
   return NR_OK;
 }
 
@@ -883,10 +898,12 @@ extern "C" nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float
     if (s->f_dbias1) cudaFree(s->f_dbias1);
     if (s->f_cam) cudaFree(s->f_cam);
     if (s->f_root) cudaFree(s->f_root);
-    s->f_G = s->f_omega = s->f_bias1 = s->f_dbias1 = s->f_root = nullptr;
+    if (s->f_omega_o) cudaFree(s->f_omega_o);
+    s->f_G = s->f_omega = s->f_bias1 = s->f_dbias1 = s->f_root = s->f_omega_o = nullptr;
     s->f_cam = nullptr;
     s->n_frames = s->frames_cap = 0;
     NR_CHECK_CUDA(cudaMalloc(&s->f_root, (size_t)n_frames * 3 * 4));
+    NR_CHECK_CUDA(cudaMalloc(&s->f_omega_o, (size_t)n_frames * 3 * kBones * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_G, G.size() * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_omega, om.size() * 4));
     NR_CHECK_CUDA(cudaMalloc(&s->f_bias1, (size_t)n_frames * kWidth * 4));

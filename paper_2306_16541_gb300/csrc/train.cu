@@ -720,7 +720,8 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
              "nr_train_step: bad Adam hyper-parameters");
   for (int k = 0; k < 4; ++k) NR_REQUIRE(b->lr_scale[k] >= 0.f, "nr_train_step: negative lr_scale");
-  NR_REQUIRE(b->loss_weight >= 0.f && b->lr_scale_refiner >= 0.f, "nr_train_step: negative loss_weight or lr scale");
+  NR_REQUIRE(b->loss_weight >= 0.f && b->lr_scale_refiner >= 0.f && b->lr_scale_cnn >= 0.f,
+             "nr_train_step: negative loss_weight or lr scale");
   if (s->n_frames == 0) {
     set_error("nr_train_step: call nr_set_frames first");
     return NR_ESTATE;
@@ -729,11 +730,11 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   cudaStream_t st = (cudaStream_t)stream;
   nr_status r;
   if ((r = prepare_params(s, st)) != NR_OK) return r;
-  if ((r = fold_frame_biases(s, st)) != NR_OK) return r;
   const bool refine = s->ref_layers != 0;
   int launched = 0;
-  if (refine) {   // every frame's G from its refined pose (Sec. 4.1)
-    if ((r = launch_refine_fk(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_G, st)) != NR_OK)
+  if (refine) {   // every frame's G and updated angles from its refined pose (Sec. 4.1)
+    if ((r = launch_refine_fk(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_G, s->f_omega_o,
+                              3 * kBones, st)) != NR_OK)
       return r;
     s->fG_refined = true;
   } else if (s->fG_refined) {   // the refiner was switched off: back to the estimated poses
@@ -741,6 +742,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
     NR_CHECK_CUDA(cudaStreamSynchronize(st));
     s->fG_refined = false;
   }
+  if ((r = fold_frame_biases(s, st)) != NR_OK) return r;
   nr_render_opts o{};
   o.mlp_dtype = NR_F32;
   o.feat_dtype = NR_F32;
@@ -842,16 +844,18 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   sa.hidden = (int)s->hidden;
   sa.mlp_in = (int)s->mlp_in;
   if (s->res_enabled) {
-    scatter_res_kernel<<<(sa.m.n_res + 255) / 256, 256, 0, st>>>(s->t_red, s->f_omega, sa, s->g_res);
+    scatter_res_kernel<<<(sa.m.n_res + 255) / 256, 256, 0, st>>>(s->t_red, refine ? s->f_omega_o : s->f_omega, sa,
+                                                                 s->g_res);
   } else {
     NR_CHECK_CUDA(cudaMemsetAsync(s->g_res, 0, s->n_res * 4, st));
   }
   scatter_mlp_kernel<<<(sa.m.n_mlp + 255) / 256, 256, 0, st>>>(s->t_red, sa, s->g_mlp);
   NR_CHECK_CUDA(cudaGetLastError());
   launched += 7;
-  if (refine && (r = launch_refine_bwd(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_dG, s->g_ref,
-                                       st)) != NR_OK)
+  if (refine && (r = launch_refine_bwd(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_dG,
+                                       s->t_red + s->lay.total, s->g_ref, st)) != NR_OK)
     return r;
+  if (s->cnn_on && (r = cnn_backward(s, st)) != NR_OK) return r;   // dL/dW^c -> CNN_skel
   if (!(b->flags & NR_GRAD_ONLY)) {
     const uint32_t mask = b->train_mask ? b->train_mask : NR_TRAIN_ALL;
     s->adam_t += 1;
@@ -868,11 +872,23 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
                    {NR_TRAIN_RES, s->res, s->g_res, s->n_res, s->n_wvol + s->n_table + s->n_mlp, b->lr_scale[3]}};
     for (const auto &g : groups) {
       if (!(mask & g.bit) || (g.bit == NR_TRAIN_RES && !s->res_enabled)) continue;
+      if (g.bit == NR_TRAIN_WVOL && s->cnn_on) continue;   // the volume is generated, not stored
       const float lr = b->lr * (g.scale > 0.f ? g.scale : 1.f);
       const int nb = (int)std::min<size_t>((g.n + 255) / 256, (size_t)blocks * 8);
       adam_kernel<<<nb, 256, 0, st>>>(g.p, g.g, s->adam_m + g.off, s->adam_v + g.off, g.n, lr, b->beta1, b->beta2,
                                       b->eps, (float)c1, (float)c2);
       ++launched;
+    }
+    if (s->cnn_on && (mask & NR_TRAIN_CNN)) {
+      s->cnn_t += 1;
+      const double q1 = 1.0 / (1.0 - pow((double)b->beta1, (double)s->cnn_t));
+      const double q2 = 1.0 / (1.0 - pow((double)b->beta2, (double)s->cnn_t));
+      const float lr = b->lr * (b->lr_scale_cnn > 0.f ? b->lr_scale_cnn : 1.f);
+      const int nb = (int)std::min<size_t>((s->n_cnn + 255) / 256, (size_t)blocks * 8);
+      adam_kernel<<<nb, 256, 0, st>>>(s->cnn, s->g_cnn, s->cnn_m, s->cnn_v, s->n_cnn, lr, b->beta1, b->beta2, b->eps,
+                                      (float)q1, (float)q2);
+      ++launched;
+      s->cnn_dirty = true;
     }
     if (refine && (mask & NR_TRAIN_REFINER)) {
       s->ref_t += 1;

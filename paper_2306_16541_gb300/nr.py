@@ -22,8 +22,9 @@ NR_F32, NR_F16, NR_BF16, NR_FP8E4M3 = range(4)
 DTYPES = {"f32": NR_F32, "f16": NR_F16, "bf16": NR_BF16, "fp8": NR_FP8E4M3}
 NR_POSE_MATRICES = 1
 NR_GRAD_ONLY = 1
-NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_REFINER, NR_TRAIN_ALL = 1, 2, 4, 8, 16, 31
-NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES, NR_PARAM_REFINER = range(5)
+NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_REFINER, NR_TRAIN_CNN = 1, 2, 4, 8, 16, 32
+NR_TRAIN_ALL = 63
+NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES, NR_PARAM_REFINER, NR_PARAM_CNN = range(6)
 # Per-group learning-rate multipliers (weight volume, hash, canonical MLP, residual MLP):
 # Sec. 5.2 uses a 10x smaller rate for the networks other than the NeRF network.
 PAPER_LR_SCALE = (0.1, 1.0, 1.0, 0.1)
@@ -70,7 +71,7 @@ class nr_train_batch(C.Structure):
                 ("step_seed", C.c_uint64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("hann_alpha", C.c_float), ("flags", C.c_uint32),
                 ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4), ("loss_weight", C.c_float),
-                ("lr_scale_refiner", C.c_float)]
+                ("lr_scale_refiner", C.c_float), ("lr_scale_cnn", C.c_float)]
 
 
 class nr_request(C.Structure):
@@ -106,6 +107,7 @@ def _load() -> C.CDLL:
         "nr_set_canonical_occupancy": ([vp, _up, C.c_float, vp], C.c_int),
         "nr_canonical_occupancy": ([vp, _up], C.c_int),
         "nr_set_pose_refiner": ([vp, C.c_uint32, C.c_uint32, _fp, vp], C.c_int),
+        "nr_set_weight_cnn": ([vp, _up, _fp, _fp, _fp, vp], C.c_int),
         "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
@@ -329,6 +331,22 @@ def nr_set_pose_refiner(h, layers, stream=None) -> None:
     check(lib.nr_set_pose_refiner(h, width, len(layers) - 1, _ptr(flat), _stream(stream)), "nr_set_pose_refiner")
 
 
+def nr_set_weight_cnn(h, layers, z=None, log_prior=None, stream=None) -> None:
+    """layers: CNN_skel as [(W_fc [C0][256], b_fc), (W_1 [C0][C1][4][4][4], b_1), ...,
+    (W_5 [C4][25][4][4][4], b_5)], or None to switch the generator off."""
+    if layers is None:
+        check(lib.nr_set_weight_cnn(h, None, None, None, None, _stream(stream)), "nr_set_weight_cnn")
+        return
+    ch = np.array([layers[0][0].shape[0]] + [W.shape[1] for W, _ in layers[1:5]], np.uint32)
+    flat = np.ascontiguousarray(np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(),
+                                                                np.asarray(b, np.float32).ravel()])
+                                                for W, b in layers]), np.float32)
+    zz = np.ascontiguousarray(z, np.float32)
+    lp = None if log_prior is None else np.ascontiguousarray(log_prior, np.float32)
+    check(lib.nr_set_weight_cnn(h, _ptr(ch, C.c_uint32), _ptr(flat), _ptr(zz),
+                                None if lp is None else _ptr(lp), _stream(stream)), "nr_set_weight_cnn")
+
+
 class Subject:
     """One performer resident on the GPU (owns an nr_subject handle)."""
 
@@ -359,7 +377,8 @@ class Subject:
     def train_step(self, frame_id, px, py, target_rgb, n_samples: int, step_seed: int, lr: float = 1e-2,
                    betas=(0.9, 0.99), eps: float = 1e-8, bg=(0.0, 0.0, 0.0), hann_alpha: float = -1.0,
                    grad_only: bool = False, train_mask: int = 0, lr_scale=(0.0, 0.0, 0.0, 0.0),
-                   loss_weight: float = 0.0, lr_scale_refiner: float = 0.0, stream=None) -> float:
+                   loss_weight: float = 0.0, lr_scale_refiner: float = 0.0, lr_scale_cnn: float = 0.0,
+                   stream=None) -> float:
         b = nr_train_batch()
         b.n_rays = int(frame_id.shape[0])
         b.frame_id = C.cast(C.c_void_p(frame_id.data_ptr()), _up)
@@ -373,6 +392,7 @@ class Subject:
         b.lr_scale[:] = [float(v) for v in lr_scale]
         b.loss_weight = float(loss_weight)
         b.lr_scale_refiner = float(lr_scale_refiner)
+        b.lr_scale_cnn = float(lr_scale_cnn)
         return nr_train_step(self.h, b, stream)
 
     def param(self, which: int):
@@ -398,6 +418,9 @@ class Subject:
 
     def set_pose_refiner(self, layers, stream=None):
         nr_set_pose_refiner(self.h, layers, stream)
+
+    def set_weight_cnn(self, layers, z=None, log_prior=None, stream=None):
+        nr_set_weight_cnn(self.h, layers, z, log_prior, stream)
 
     def canonical_occupancy(self):
         return nr_canonical_occupancy(self.h, self.occ_grid)

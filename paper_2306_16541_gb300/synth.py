@@ -360,6 +360,26 @@ def refiner_layers(seed: int, width: int = 256, hidden_layers: int = 4, last_std
     return kaiming_layers(rng, refiner_dims(width, hidden_layers), last_std=last_std)
 
 
+def cnn_layers(seed: int, channels=(1024, 512, 256, 128, 64), last_std: float = 1e-2):
+    """Seeded CNN_skel weights: the fully-connected layer and five transposed convolutions
+    (He-normal over each output's fan-in: 256, and C_in x 8 taps), zero biases; a small last
+    layer so that the generated volume starts near softmax(log prior)."""
+    rng = np.random.default_rng(seed)
+    out = [((rng.normal(0.0, math.sqrt(2.0 / 256), size=(channels[0], 256))).astype(np.float32),
+            np.zeros(channels[0], np.float32))]
+    ins = list(channels)
+    outs = list(channels[1:]) + [N_BONES + 1]
+    for k, (ci, co) in enumerate(zip(ins, outs)):
+        std = last_std if k == 4 else math.sqrt(2.0 / (ci * 8))
+        out.append((rng.normal(0.0, std, size=(ci, co, 4, 4, 4)).astype(np.float32), np.zeros(co, np.float32)))
+    return out
+
+
+def cnn_latent(seed: int) -> np.ndarray:
+    """The constant random latent z [256] of CNN_skel."""
+    return np.random.default_rng(seed).normal(size=256).astype(np.float32)
+
+
 def shaped_density(subj: dict, beta: float = 8.0, bias: float = -4.0, keep_ellipsoids: bool = False) -> dict:
     """A copy of `subj` (made with ellipsoids) whose canonical density follows the performer's body.
 

@@ -66,8 +66,7 @@ def test_refined_transforms_match_oracle(width, hidden):
 def test_render_with_refiner_matches_oracle():
     nr = nrmod()
     cfg = synth.config_tiny()
-    s = dict(cfg["subject"])
-    s["hash_table"] = synth.subject(64, hash_scale=0.5)["hash_table"]
+    s = synth.subject(64, hash_scale=0.5, res_last_std=0.02)    # MLP_res sees the updated angles
     layers = _refiner(65)
     cam = synth.camera(32, 32, 40.0, (0.0, 0.0, 2.5), 24, 1.5, 3.5)
     S = nr.Subject(s)
@@ -86,9 +85,10 @@ def test_render_with_refiner_matches_oracle():
     assert ref[:, 3].max() > 0.1                       # the performer is in view
 
 
-def _linear_subject(seed):
-    """Kink-free encoding (linear dense levels): the gradient has no float32/float64 cell flips."""
-    s = synth.subject(seed, hash_scale=0.5)
+def _linear_subject(seed, res_std=0.02):
+    """Kink-free encoding (linear dense levels): the gradient has no float32/float64 cell flips.
+    A non-zero residual output carries dL/dOmega^o back to the refiner."""
+    s = synth.subject(seed, hash_scale=0.5, res_last_std=res_std)
     s["hash_levels"], s["level_res"], s["log2_T"] = 2, np.array([4, 8], np.uint32), 10
     tab = np.zeros((2, 1 << 10, 2), np.float32)
     rng = np.random.default_rng(seed)
@@ -125,11 +125,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("n_frames,S_", [(3, 16), (20, 12)])
-def test_refiner_gradient_matches_oracle(n_frames, S_):
+@pytest.mark.parametrize("n_frames,S_,res_std", [(3, 16, 0.02), (20, 12, 0.02), (3, 16, 0.3)])
+def test_refiner_gradient_matches_oracle(n_frames, S_, res_std):
     """dL/dtheta through the per-sample dL/dp_i, the per-frame reduction to dL/dG_i (shared
-    memory for up to 16 frames, global atomics beyond), the kinematic chain and MLP_theta."""
-    subj = _linear_subject(66)
+    memory for up to 16 frames, global atomics beyond), the kinematic chain and MLP_theta,
+    plus the residual MLP's conditioning on Omega^o through the rotation log (about 3 % of
+    the gradient's norm with the strong residual, 0.4 % with the weak one)."""
+    subj = _linear_subject(66, res_std)
     layers = _refiner(67)
     frames = synth.training_frames(68, n_frames, res=32)
     for c in frames["cameras"]:

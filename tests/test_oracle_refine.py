@@ -35,6 +35,34 @@ def test_rotation_derivative_at_zero_is_the_generator():
         assert np.allclose(J[:, :, a].numpy(), gen, atol=1e-15)
 
 
+def test_rotation_log_matches_scipy_and_inverts_rodrigues():
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(9)
+    axis = rng.normal(size=(30, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    ang = np.concatenate([rng.uniform(0, 3.0, 25), [1e-9, 1e-6, 1e-4, 0.0, 2.9]])
+    v = axis * ang[:, None]
+    R = fk.rodrigues(v)
+    got = refine.rot_log_t(torch.from_numpy(R)).numpy()
+    assert np.allclose(got, Rot.from_matrix(R).as_rotvec(), atol=1e-9)
+    assert np.allclose(got, v, atol=1e-9)
+
+
+def test_updated_angles_of_a_fixed_correction():
+    """Omega^o of joint j >= 1 is the rotation vector of Rot(Delta_j) Rot(omega_j) (scipy); the
+    root keeps omega_0."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    s = synth.subject(5)
+    aa, rt = synth.random_pose(np.random.default_rng(6))
+    delta = np.random.default_rng(10).normal(scale=0.2, size=(23, 3))
+    layers = _layers(8)
+    layers[-1] = (torch.zeros_like(layers[-1][0]), torch.from_numpy(delta.reshape(-1)))
+    _, _, om = refine.refined_pose(s["parents"], s["rest_joints"], aa, rt, layers)
+    ref = np.asarray(aa, np.float64).copy()
+    ref[1:] = (Rot.from_rotvec(delta) * Rot.from_rotvec(ref[1:])).as_rotvec()
+    assert np.allclose(om.numpy().reshape(-1, 3), ref, atol=1e-12)
+
+
 def test_without_refiner_is_the_numpy_fk():
     s = synth.subject(3)
     aa, rt = synth.random_pose(np.random.default_rng(4))
