@@ -150,13 +150,15 @@ def cpu_baseline(cfg, poses, n_pixels, seed=0):
                        f"FP64 torch CPU, no early termination), {dt:.1f} s")
 
 
-def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform"):
+def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform", full=False):
     """Training-step time on the training workload: 16 frames of 512x512 with seeded
     poses, targets rendered from a seeded ground-truth field of the tiny workload's
     shape, 2^18 random pixel rays x 128 stratified samples, forward + backward +
     Adam (lr 1e-2, beta (0.9, 0.99)).  CUDA events on the training stream.
     layout "patch" draws the rays as 6 patches of 20x20 pixels per image (110 images,
-    264,000 rays) and weights the MSE by 0.2 (Sec. 5.2)."""
+    264,000 rays) and weights the MSE by 0.2 (Sec. 5.2).  full: the whole motion model of
+    Sec. 4 is trained as well -- the pose refiner MLP_theta (4 x 256) and the weight volume
+    generated by CNN_skel (channels 1024-512-256-128-64, prior = the initial volume)."""
     import torch
     from paper_2306_16541_gb300 import synth
     gt = synth.subject(700, hash_scale=0.5, res_last_std=0.02)
@@ -173,6 +175,10 @@ def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform"):
     targets = torch.stack(targets)
     Sub = nr.Subject(trainee, device=device)
     Sub.set_frames(frames["axis_angle"], frames["root_t"], frames["cameras"])
+    if full:
+        Sub.set_pose_refiner(synth.refiner_layers(703))
+        Sub.set_weight_cnn(synth.cnn_layers(704), synth.cnn_latent(705),
+                           np.log(np.asarray(trainee["wvol"], np.float64) + 1e-6).astype(np.float32))
     gen = torch.Generator(device="cuda").manual_seed(702)
     batches = []
     weight = 0.0
@@ -205,12 +211,59 @@ def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform"):
         ms.append(e0.elapsed_time(e1))
     Sub.close()
     shape = "6 patches of 20x20 per image, MSE weight 0.2" if layout == "patch" else "uniform pixels"
-    return {"workload": f"16 frames 512x512, {n} rays ({shape}) x 128 samples, fp32 forward+backward+Adam",
+    extra = ", pose refiner 4x256 + CNN_skel 1024-512-256-128-64" if full else ""
+    return {"workload": f"16 frames 512x512, {n} rays ({shape}) x 128 samples, fp32 forward+backward+Adam{extra}",
             "lr": "1e-2 (hash, canonical MLP), 1e-3 (weight volume, residual MLP)",
             "ms": statistics.mean(ms), "ms_min": min(ms), "steps": steps, "warmup": warmup,
             "rays_per_s": n / (statistics.mean(ms) / 1000.0),
             "samples_per_s": n * 128 / (statistics.mean(ms) / 1000.0),
             "loss_first": losses[0], "loss_last": losses[-1]}
+
+
+def occupancy_bench(nr, device, mlp, steps=5):
+    """Density-grid occupancy (Sec. 2.3 for subjects without ellipsoids) on the frame workload's
+    field with a body-shaped density: the canonical refresh (sigma at 128^3 cell centres,
+    threshold 1e-3, dilation 1), the posing through the warp (128^3 cells), and a 512x512x128
+    frame rendered with the grid, against the same frame without skipping."""
+    import torch
+    from paper_2306_16541_gb300 import synth
+    cfg = synth.config_frame512()
+    subj = synth.shaped_density(cfg["subject"])
+    S = nr.Subject(subj, device=device)
+    cam = nr.make_camera(cfg["camera"])
+    out = torch.empty(cam.height, cam.width, 4, device="cuda")
+    rng = np.random.default_rng(3300)
+    poses = [synth.random_pose(rng) for _ in range(steps + 1)]
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    S.set_pose(*poses[0])
+    S.refresh_occupancy(1e-3, 1)
+    S.occupancy()
+    refresh = [timed(lambda: S.refresh_occupancy(1e-3, 1)) for _ in range(steps)]
+    pose_ms, frame_grid, frame_full, live_grid, live_full = [], [], [], [], []
+    opts_g = nr.make_opts(mlp, "f16", True, 1e-4, profile=True)
+    opts_n = nr.make_opts(mlp, "f16", False, 1e-4, profile=True)
+    for p in poses[1:]:
+        S.set_pose(*p)
+        pose_ms.append(timed(lambda: S.occupancy()))          # posing + a 256 KiB readback
+        frame_grid.append(timed(lambda: S.render(cam, opts_g, out)))
+        live_grid.append(S.stage_times()["live_samples"])
+        frame_full.append(timed(lambda: S.render(cam, opts_n, out)))
+        live_full.append(S.stage_times()["live_samples"])
+    S.close()
+    n_rays = cam.width * cam.height
+    return {"workload": "frame 512x512x128 field with body-shaped density, canonical and posed grids 128^3",
+            "refresh_ms": statistics.mean(refresh), "pose_ms": statistics.mean(pose_ms),
+            "frame_ms_grid": statistics.mean(frame_grid), "frame_ms_no_skip": statistics.mean(frame_full),
+            "rays_per_s_grid": n_rays / (statistics.mean(frame_grid) / 1000.0),
+            "live_samples_grid": statistics.mean(live_grid), "live_samples_no_skip": statistics.mean(live_full)}
 
 
 def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slots=16):
@@ -434,6 +487,9 @@ def run_ours(a):
     e2e_value = world * n_rays * a.steps / e2e_s
 
     train = train_bench(nr, local, a.train_steps, n=a.train_rays, layout=a.train_layout) if a.train_steps > 0 else None
+    train_full = (train_bench(nr, local, max(2, a.train_steps // 2), n=a.train_rays, layout="patch", full=True)
+                  if a.train_steps > 0 else None)
+    occupancy = occupancy_bench(nr, local, a.mlp) if a.train_steps > 0 else None
     serving = serve_bench(nr, local, a.mlp, duration=a.serve_seconds) if a.serve_seconds > 0 else None
     sweep = sweep_bench(nr, local) if (a.sweep and rank == 0) else None
 
@@ -474,6 +530,8 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},
         "train_step": train,
+        "train_step_full_model": train_full,
+        "occupancy_grid": occupancy,
         "serving": serving,
         "precision_sweep": sweep,
         "gpu_launches": launches,

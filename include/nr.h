@@ -189,7 +189,8 @@ typedef struct {
   uint32_t use_occupancy;  /* skip samples whose posed occupancy cell is empty */
   float t_min;             /* early ray termination once transmittance < t_min; 0 = off */
   float hann_alpha;        /* residual PE window position; < 0 = all bands */
-  uint32_t flags;          /* NR_RENDER_PROFILE | NR_RENDER_TCGEN05 | NR_RENDER_MMA2, or 0 */
+  uint32_t flags;          /* NR_RENDER_PROFILE | NR_RENDER_TCGEN05 | NR_RENDER_MMA2 |
+                              NR_RENDER_ALL_BONES, or 0 */
 } nr_render_opts;
 
 /* Renders the current pose from `cam` into out_rgba[height][width][4]
@@ -391,6 +392,10 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
                                  accumulators (M = 128 tiles) instead of warp-level mma.sync */
 #define NR_RENDER_MMA2 4u     /* nr_render_opts.flags: warp-level mma.sync over two 16-row tiles per
                                  weight-fragment read (12 warps/SM instead of 16) */
+#define NR_RENDER_ALL_BONES 8u /* nr_render_opts.flags: evaluate all 24 bone channels at every sample.
+                                 By default a candidate G_i x is skipped when its trilinear cell lies
+                                 outside the index box of channel i's vertices above 1e-7 (weights
+                                 that small change S by at most 2.4e-6); training never skips. */
 
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,

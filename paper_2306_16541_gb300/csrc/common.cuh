@@ -15,6 +15,8 @@
 namespace nr {
 
 constexpr int kBones = 24;
+constexpr int kPoseSmem = kBones * 12 + kBones * 6;   // bone transforms then support boxes (floats)
+constexpr float kBoneEps = 1e-7f;   // bone-channel values at or below this are skipped when rendering
 constexpr int kWidth = 64;          // hidden width of both MLPs
 constexpr int kMlpIn = 32;          // canonical MLP input (hash features, zero-padded)
 constexpr int kMaxLevels = 16;
@@ -92,6 +94,7 @@ struct FieldParams {
   const float *fp8_scales;           // its weight and activation scales
   const uint8_t *t5_bf16, *t5_f16;   // swizzled K-major weight blobs of the tcgen05 path (field_t5.cu)
   uint32_t *t5_err;                  // set by the tcgen05 path when a bounded wait gives up
+  const float *bone_box;             // [24][6] per-bone support box in volume-index units, or NULL
   // occupancy from the field's density (kModeDensity / kModePose of the FP32 kernel)
   int occ_grid;                      // cells per axis
   float occ_tau;                     // density threshold
@@ -138,6 +141,8 @@ struct nr_subject {
   __half2 *table16 = nullptr;
   float *blob = nullptr;
   float4 *wquad = nullptr;           // corner-block copy of the bone channels of wvol
+  float *bone_box = nullptr;         // [24][6] support boxes of the bone channels (render skip)
+  int *bone_ibox = nullptr;          // [24][6] their voxel bounds
   nr::BlobLayout lay{};
   __nv_bfloat16 *tc_bf16 = nullptr;
   __half *tc_f16 = nullptr;

@@ -59,9 +59,24 @@ __device__ __forceinline__ float trilinear_quad_grad(const float4 *__restrict__ 
 
 __host__ __device__ inline size_t quad_channel(int R) { return (size_t)(R + 2) * (R + 1) * (R + 1); }
 
+// Stages the pose (and, when P.bone_box is set, the support boxes) into shared
+// memory at sG [kPoseSmem]; returns the box pointer to pass to lbs_warp.
+__device__ __forceinline__ const float *stage_pose(const FieldParams &P, float *sG, int tid, int nthreads) {
+  for (int i = tid; i < kBones * 12; i += nthreads) sG[i] = P.G[i];
+  if (!P.bone_box) return nullptr;
+  for (int i = tid; i < kBones * 6; i += nthreads) sG[kBones * 12 + i] = P.bone_box[i];
+  return sG + kBones * 12;
+}
+
 // sG: the 24 bone transforms [24][12] (rows [R | t]) in shared memory.
+// sBox (render kernels, may be NULL): per bone (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z) in
+// volume-index units such that every vertex of the channel above kBoneEps lies in
+// [lo + 1, hi - 1]; a candidate with u outside [lo, hi) has all eight corners at or below
+// kBoneEps and is skipped (its weight counts as 0).  Skipping changes S by at most
+// 24 kBoneEps and x_skel by at most 24 kBoneEps |p_i - x_skel| / S.
 __device__ __forceinline__ void lbs_warp(const FieldParams &P, const float *__restrict__ sG, float x0, float x1,
-                                         float x2, float &s0, float &s1, float &s2, float &S) {
+                                         float x2, float &s0, float &s1, float &s2, float &S,
+                                         const float *__restrict__ sBox = nullptr) {
   const int R = P.wres;
   const size_t QC = quad_channel(R);
   float n0 = 0.f, n1 = 0.f, n2 = 0.f, sum = 0.f;
@@ -74,6 +89,10 @@ __device__ __forceinline__ void lbs_warp(const FieldParams &P, const float *__re
     const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
     const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
     const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
+    if (sBox) {
+      const float *b = sBox + 6 * i;
+      if (ux < b[0] || uy < b[1] || uz < b[2] || ux >= b[3] || uy >= b[4] || uz >= b[5]) continue;
+    }
     const float w = trilinear_quad(P.wquad + (size_t)i * QC, R, ux, uy, uz);
     sum += w;
     n0 = fmaf(w, p0, n0);
@@ -166,6 +185,34 @@ __device__ __forceinline__ float2 table_read(const FieldParams &P, int l, uint32
   return __ldg(P.table32 + off);
 }
 
+// The two features of level l at the clamped box coordinate p: 8 corners read
+// trilinearly from the f16 or f32 table (the dtype test sits outside the corners).
+__device__ __forceinline__ void hash_level(const FieldParams &P, int l, float p0, float p1, float p2, float &fa,
+                                           float &fb) {
+  HashCell c;
+  hash_cell(P, l, p0, p1, p2, c);
+  fa = 0.f;
+  fb = 0.f;
+  const size_t base = (size_t)l * (size_t)(P.T_mask + 1);
+  if (P.use_f16_table) {
+    const __half2 *tab = P.table16 + base;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 v = __half22float2(tab[c.idx[k]]);
+      fa = fmaf(c.w[k], v.x, fa);
+      fb = fmaf(c.w[k], v.y, fb);
+    }
+  } else {
+    const float2 *tab = P.table32 + base;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 v = __ldg(tab + c.idx[k]);
+      fa = fmaf(c.w[k], v.x, fa);
+      fb = fmaf(c.w[k], v.y, fb);
+    }
+  }
+}
+
 // enc (a column with the given stride): 2 features per level, zero beyond 2L.  Returns whether x is inside the box.
 __device__ __forceinline__ bool hash_encode(const FieldParams &P, float x0, float x1, float x2, float *__restrict__ enc,
                                             int stride) {
@@ -176,21 +223,17 @@ __device__ __forceinline__ bool hash_encode(const FieldParams &P, float x0, floa
   p0 = fminf(fmaxf(p0, 0.f), 1.f);
   p1 = fminf(fmaxf(p1, 0.f), 1.f);
   p2 = fminf(fmaxf(p2, 0.f), 1.f);
-#pragma unroll
-  for (int l = 0; l < kMaxLevels; ++l) {
-    float a = 0.f, b = 0.f;
-    if (l < P.L) {
-      HashCell c;
-      hash_cell(P, l, p0, p1, p2, c);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float2 v = table_read(P, l, c.idx[k]);
-        a = fmaf(c.w[k], v.x, a);
-        b = fmaf(c.w[k], v.y, b);
-      }
-    }
+  // a runtime level loop: one copy of the level body keeps the kernels' code small
+#pragma unroll 1
+  for (int l = 0; l < P.L; ++l) {
+    float a, b;
+    hash_level(P, l, p0, p1, p2, a, b);
     enc[(2 * l) * stride] = inside ? a : 0.f;
     enc[(2 * l + 1) * stride] = inside ? b : 0.f;
+  }
+  for (int l = P.L; l < kMaxLevels; ++l) {
+    enc[(2 * l) * stride] = 0.f;
+    enc[(2 * l + 1) * stride] = 0.f;
   }
   return inside;
 }

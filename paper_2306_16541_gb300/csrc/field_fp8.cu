@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(kF8Threads, 1) field_fp8_kernel(FieldParams P,
   float *sBias = reinterpret_cast<float *>(smem + ((fl.total + 15) & ~15));
   float *sS = sBias + ((bl.total + 3) & ~3);                              // scales
   float *sG = sS + ((kFp8Scales + 3) & ~3);
-  uint8_t *sGam = reinterpret_cast<uint8_t *>(sG + kBones * 12);           // [warps][32][kF8Row]
+  uint8_t *sGam = reinterpret_cast<uint8_t *>(sG + kPoseSmem);             // [warps][32][kF8Row]
   uint8_t *sH = sGam + kF8Warps * 32 * kF8Row;                             // [warps][32][kF8Row]
   float *sOut = reinterpret_cast<float *>(sH + kF8Warps * 32 * kF8Row);   // [warps][32][4]
+  const float *sBox = nullptr;
   {
     const int4 *src = reinterpret_cast<const int4 *>(Q.blob);
     int4 *dst = reinterpret_cast<int4 *>(sW);
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kF8Threads, 1) field_fp8_kernel(FieldParams P,
     for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.c0 + kWidth * (l + 1), P.blob + P.lay.chb[l], kWidth, kWidth);
     copyb(bl.cl, P.blob + P.lay.clb, 4, 8);
     for (int i = threadIdx.x; i < kFp8Scales; i += blockDim.x) sS[i] = Q.scales[i];
-    for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
+    sBox = stage_pose(P, sG, threadIdx.x, blockDim.x);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kF8Threads, 1) field_fp8_kernel(FieldParams P,
       }
     }
     float s0, s1, s2, S;
-    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
+    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S, sBox);
     float f0 = s0, f1 = s1, f2 = s2;
     if (P.res_enabled) {
       {  // gamma(x_skel) quantised with 1 / s_gamma into the lane's row (48 values, zero to 64)
@@ -279,21 +280,13 @@ __global__ void __launch_bounds__(kF8Threads, 1) field_fp8_kernel(FieldParams P,
       p2 = fminf(fmaxf(p2, 0.f), 1.f);
       const float ie = 1.f / sS[SA_ENC];
       uint16_t *row = reinterpret_cast<uint16_t *>(hh + lane * kF8Row);
-#pragma unroll
-      for (int l = 0; l < kMaxLevels; ++l) {
-        float fa = 0.f, fb = 0.f;
-        if (l < P.L) {
-          HashCell c;
-          hash_cell(P, l, p0, p1, p2, c);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float2 v = table_read(P, l, c.idx[k]);
-            fa = fmaf(c.w[k], v.x, fa);
-            fb = fmaf(c.w[k], v.y, fb);
-          }
-        }
+#pragma unroll 1
+      for (int l = 0; l < P.L; ++l) {
+        float fa, fb;
+        hash_level(P, l, p0, p1, p2, fa, fb);
         row[l] = inside ? to_e4m3x2(fa * ie, fb * ie) : (uint16_t)0;
       }
+      for (int l = P.L; l < kMaxLevels; ++l) row[l] = (uint16_t)0;
     }
     __syncwarp();
 #pragma unroll 1
@@ -515,7 +508,7 @@ static nr_status launch_fp8_mode(const FieldParams &P, const Fp8Params &Q, const
   const Fp8Layout fl = fp8_layout(P.hidden);
   const TcBias bl = tc_bias_layout(P.hidden);
   size_t smem = (size_t)((fl.total + 15) & ~15);
-  smem += sizeof(float) * (((bl.total + 3) & ~3) + ((kFp8Scales + 3) & ~3) + kBones * 12);
+  smem += sizeof(float) * (((bl.total + 3) & ~3) + ((kFp8Scales + 3) & ~3) + kPoseSmem);
   smem += (size_t)kF8Warps * 32 * kF8Row * 2 + sizeof(float) * kF8Warps * 32 * 4;
   NR_CHECK_CUDA(cudaFuncSetAttribute(field_fp8_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   field_fp8_kernel<MODE><<<num_sms(device), kF8Threads, smem, st>>>(P, Q, in, n_fixed, n_dev, out);

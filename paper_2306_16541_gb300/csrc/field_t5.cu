@@ -223,10 +223,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) field_t5_kernel(FieldParams P, 
   uint8_t *sTiles = sW + ((L.total + 1023) & ~1023);                  // [group][gamma 16 KB | h 16 KB]
   float *sBias = reinterpret_cast<float *>(sTiles + kT5Groups * 32768);
   float *sG = sBias + ((bl.total + 3) & ~3);
-  uint64_t *sMbar = reinterpret_cast<uint64_t *>(sG + kBones * 12);
+  uint64_t *sMbar = reinterpret_cast<uint64_t *>(sG + kPoseSmem);
   uint32_t *sTmem = reinterpret_cast<uint32_t *>(sMbar + kT5Groups);
 
   const int tid = threadIdx.x, warp = tid >> 5, group = warp >> 2, r = tid & 127;
+  const float *sBox = nullptr;
   {
     const int4 *src = reinterpret_cast<const int4 *>(wblob);
     int4 *dst = reinterpret_cast<int4 *>(sW);
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) field_t5_kernel(FieldParams P, 
     copyb(bl.c0, P.blob + P.lay.c0b, kWidth, kWidth);
     for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.c0 + kWidth * (l + 1), P.blob + P.lay.chb[l], kWidth, kWidth);
     copyb(bl.cl, P.blob + P.lay.clb, 4, 4);
-    for (int i = tid; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
+    sBox = stage_pose(P, sG, tid, blockDim.x);
     if (tid < kT5Groups) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(sMbar + tid)));
     if (warp == 0) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) field_t5_kernel(FieldParams P, 
       }
     }
     float s0, s1, s2, S;
-    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
+    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S, sBox);
     float f0 = s0, f1 = s1, f2 = s2;
     float acc[64];
     if (P.res_enabled) {
@@ -449,7 +450,7 @@ static size_t t5_smem(int hidden) {
   const T5Layout L = t5_layout(hidden);
   const TcBias bl = tc_bias_layout(hidden);
   size_t b = 1024 + (size_t)((L.total + 1023) & ~1023) + (size_t)kT5Groups * 32768;
-  b += sizeof(float) * (((bl.total + 3) & ~3) + kBones * 12);
+  b += sizeof(float) * (((bl.total + 3) & ~3) + kPoseSmem);
   b += sizeof(uint64_t) * kT5Groups + 16;
   return b;
 }

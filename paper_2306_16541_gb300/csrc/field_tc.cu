@@ -20,7 +20,7 @@ namespace nr {
 // Threads per block for MT m-tiles per weight-fragment read (one block per SM).
 template <int MT>
 struct TcCfg {
-  static constexpr int threads = MT == 1 ? 512 : 384;
+  static constexpr int threads = MT == 1 ? 640 : 384;
   static constexpr int warps = threads / 32;
 };
 constexpr int kGamRow = kResGammaPad + 8;   // 56: gamma tile row stride (elements)
@@ -37,9 +37,10 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
   float *sG = sBias + ((bl.total + 3) & ~3);
   // per warp: one [32][kGamRow] tile that holds gamma(x_skel) for the residual MLP and,
   // once that is done, the hash encoding (row stride kEncRow) for the canonical MLP
-  T *sGam = reinterpret_cast<T *>(sG + kBones * 12);                     // [warps][32][kGamRow]
+  T *sGam = reinterpret_cast<T *>(sG + kPoseSmem);                       // [warps][32][kGamRow]
   float *sOut = reinterpret_cast<float *>(sGam + TcCfg<MT>::warps * 32 * kGamRow);  // [warps][32][4]
 
+  const float *sBox = nullptr;
   {  // stage weights, biases and the pose's bone transforms
     const int4 *src = reinterpret_cast<const int4 *>(P.tc_blob);
     int4 *dst = reinterpret_cast<int4 *>(sW);
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
     copyb(bl.c0, P.blob + P.lay.c0b, kWidth, kWidth);
     for (int l = 0; l < P.hidden - 1; ++l) copyb(bl.c0 + kWidth * (l + 1), P.blob + P.lay.chb[l], kWidth, kWidth);
     copyb(bl.cl, P.blob + P.lay.clb, 4, 8);
-    for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
+    sBox = stage_pose(P, sG, threadIdx.x, blockDim.x);
   }
   __syncthreads();
 
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
       }
     }
     float s0, s1, s2, S;
-    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
+    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S, sBox);
     float f0 = s0, f1 = s1, f2 = s2;
     if (P.res_enabled) {
       {  // gamma(x_skel) as one row of the warp's tile
@@ -126,12 +127,12 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
         init_bias(sBias + bl.r1, acc);
         mma_block<T, 3, 8, MT>(ag, sW + P.tlay.r1, kTcRow, 0, acc);
         relu_to_a<T, MT>(acc, a);
-        init_bias(sBias + bl.r2, acc);
-        mma_block<T, 4, 8, MT>(a, sW + P.tlay.r2, kTcRow, 0, acc);
-        relu_to_a<T, MT>(acc, a);
-        init_bias(sBias + bl.r3, acc);
-        mma_block<T, 4, 8, MT>(a, sW + P.tlay.r3, kTcRow, 0, acc);
-        relu_to_a<T, MT>(acc, a);
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {   // layers 2 and 3 share one copy of the code
+          init_bias(sBias + (q ? bl.r3 : bl.r2), acc);
+          mma_block<T, 4, 8, MT>(a, sW + (q ? P.tlay.r3 : P.tlay.r2), kTcRow, 0, acc);
+          relu_to_a<T, MT>(acc, a);
+        }
         init_bias(sBias + bl.r4, acc);                               // layer 4 sees [h3, gamma]
         mma_block<T, 4, 8, MT>(a, sW + P.tlay.r4, kTcRowWide, 0, acc);
         mma_block<T, 3, 8, MT>(ag, sW + P.tlay.r4, kTcRowWide, kWidth, acc);
@@ -158,21 +159,14 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
       p1 = fminf(fmaxf(p1, 0.f), 1.f);
       p2 = fminf(fmaxf(p2, 0.f), 1.f);
       uint32_t *row = reinterpret_cast<uint32_t *>(enc + lane * kEncRow);
-#pragma unroll
-      for (int l = 0; l < kMaxLevels; ++l) {
-        float fa = 0.f, fb = 0.f;
-        if (l < P.L) {
-          HashCell c;
-          hash_cell(P, l, p0, p1, p2, c);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float2 v = table_read(P, l, c.idx[k]);
-            fa = fmaf(c.w[k], v.x, fa);
-            fb = fmaf(c.w[k], v.y, fb);
-          }
-        }
+      // one copy of the level body (a runtime loop keeps the kernel's code small)
+#pragma unroll 1
+      for (int l = 0; l < P.L; ++l) {
+        float fa, fb;
+        hash_level(P, l, p0, p1, p2, fa, fb);
         row[l] = inside ? TcOps<T>::pack(fa, fb) : 0u;
       }
+      for (int l = P.L; l < kMaxLevels; ++l) row[l] = 0u;
     }
     __syncwarp();
 #pragma unroll 1
@@ -215,7 +209,7 @@ template <typename T, int MT>
 static size_t tc_smem(const FieldParams &P) {
   const TcBias bl = tc_bias_layout(P.hidden);
   size_t b = ((P.tlay.total * sizeof(T) + 15) & ~size_t(15));
-  b += sizeof(float) * (((bl.total + 3) & ~3) + kBones * 12);
+  b += sizeof(float) * (((bl.total + 3) & ~3) + kPoseSmem);
   b += sizeof(T) * (size_t)TcCfg<MT>::warps * 32 * kGamRow;
   b += sizeof(float) * (size_t)TcCfg<MT>::warps * 32 * 4;
   return b;

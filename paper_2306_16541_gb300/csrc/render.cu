@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
   extern __shared__ float4 smem4[];
   float *sW = reinterpret_cast<float *>(smem4);
   float *sG = sW + P.lay.total;
-  float *sB1 = sG + kBones * 12;
+  float *sB1 = sG + kPoseSmem;
   float *sCol = sB1 + kWidth;
   for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
     reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
-  for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = P.G[i];
+  const float *sBox = stage_pose(P, sG, threadIdx.x, blockDim.x);
   for (int i = threadIdx.x; i < kWidth; i += blockDim.x) sB1[i] = P.bias1[i];
   __syncthreads();
   const int stride = blockDim.x;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
       continue;
     }
     float s0, s1, s2, S;
-    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S);
+    lbs_warp(P, sG, x0, x1, x2, s0, s1, s2, S, sBox);
     float f0 = s0, f1 = s1, f2 = s2;
     if (MODE == kModePose) {
       bool occ = false;
@@ -375,7 +375,7 @@ __global__ void finalize_rays_kernel(const float4 *__restrict__ state, uint32_t 
 }
 
 size_t field_f32_smem(const FieldParams &P) {
-  return sizeof(float) * (P.lay.total + kBones * 12 + kWidth + (size_t)kF32ColRows * kF32Threads);
+  return sizeof(float) * (P.lay.total + kPoseSmem + kWidth + (size_t)kF32ColRows * kF32Threads);
 }
 
 int num_sms(int device) {

@@ -109,10 +109,9 @@ void forward_kinematics(const nr_subject *s, const float *aa, const float *root_
 __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__restrict__ G, const float *__restrict__ E,
                                                              float bx, float by, float bz, float Bx, float By,
                                                              float Bz, int grid, uint32_t *__restrict__ bits) {
-  __shared__ float sG[kBones * 12], sE[kBones * 15];
+  __shared__ float sG[kBones * 12], sE[kBones * 15], sC[kBones * 4];
   for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = G[i];
   for (int i = threadIdx.x; i < kBones * 15; i += blockDim.x) sE[i] = E[i];
-  __syncthreads();
   const uint32_t n = (uint32_t)grid * grid * grid;
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   const float fg = (float)grid;
@@ -122,6 +121,30 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
   // 0.5 sqrt(((h0 h0) + (h1 h1)) + (h2 h2))
   const float dil = __fmul_rn(0.5f, __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(h0, h0), __fmul_rn(h1, h1)),
                                                          __fmul_rn(h2, h2))));
+  __syncthreads();
+  // A filter that never changes the decision: G_i is rigid, so a centre passing the
+  // test lies within the largest dilated radius rho_i of ellipsoid i's centre mapped to
+  // the observation space, c_i = R_i^T (centre_i - t_i); with a 1 mm margin far above
+  // float32 rounding, a centre farther than that skips the exact test.
+  if (threadIdx.x < kBones) {
+    const int i = threadIdx.x;
+    const float *g = sG + 12 * i;
+    const float *e = sE + 15 * i;
+    const float d0 = e[0] - g[3], d1 = e[1] - g[7], d2 = e[2] - g[11];
+    sC[4 * i + 0] = g[0] * d0 + g[4] * d1 + g[8] * d2;
+    sC[4 * i + 1] = g[1] * d0 + g[5] * d1 + g[9] * d2;
+    sC[4 * i + 2] = g[2] * d0 + g[6] * d1 + g[10] * d2;
+    const float rho = fmaxf(fmaxf(e[12], e[13]), e[14]) + dil + 1e-3f;
+    // only for a rotation (transforms given as matrices need not be rigid): |R^T R - I| small
+    float dev = 0.f;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const float rr = g[a] * g[b] + g[4 + a] * g[4 + b] + g[8 + a] * g[8 + b];
+        dev = fmaxf(dev, fabsf(rr - (a == b ? 1.f : 0.f)));
+      }
+    sC[4 * i + 3] = dev < 1e-4f ? rho * rho : INFINITY;
+  }
+  __syncthreads();
   bool occ = false;
   if (c < n) {
     const int cx = (int)(c % grid), cy = (int)((c / grid) % grid), cz = (int)(c / (grid * grid));
@@ -130,6 +153,9 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
     const float y1 = __fadd_rn(by, __fmul_rn(__fadd_rn((float)cy, 0.5f), h1));
     const float y2 = __fadd_rn(bz, __fmul_rn(__fadd_rn((float)cz, 0.5f), h2));
     for (int i = 0; i < kBones && !occ; ++i) {
+      const float *sc = sC + 4 * i;
+      const float a0 = y0 - sc[0], a1 = y1 - sc[1], a2 = y2 - sc[2];
+      if (a0 * a0 + a1 * a1 + a2 * a2 > sc[3]) continue;
       const float *g = sG + 12 * i;
       const float *e = sE + 15 * i;
       float v[3];
@@ -156,6 +182,43 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
   }
   const unsigned word = __ballot_sync(0xffffffffu, occ);
   if ((threadIdx.x & 31) == 0 && c < n) bits[c >> 5] = word;
+}
+
+// ------------------------------------------------------ bone support boxes
+// For each bone channel, the index bounds of the vertices whose weight exceeds
+// kBoneEps; rendering skips a candidate whose trilinear cell lies outside them.
+__global__ void bone_box_init_kernel(int *ibox, int R) {
+  const int i = threadIdx.x;
+  if (i < kBones * 6) ibox[i] = (i % 6) < 3 ? R : -1;
+}
+
+__global__ void bone_box_kernel(const float *__restrict__ wvol, int R, int *__restrict__ ibox) {
+  const size_t R3 = (size_t)R * R * R;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kBones * R3) return;
+  if (!(wvol[idx] > kBoneEps)) return;
+  const int c = (int)(idx / R3);
+  const int v = (int)(idx % R3);
+  const int x = v % R, y = (v / R) % R, z = v / (R * R);
+  int *b = ibox + 6 * c;
+  atomicMin(b + 0, x);
+  atomicMin(b + 1, y);
+  atomicMin(b + 2, z);
+  atomicMax(b + 3, x);
+  atomicMax(b + 4, y);
+  atomicMax(b + 5, z);
+}
+
+// u in [lo - 1, hi + 1) may touch a vertex in [lo, hi]; an empty channel skips everywhere
+__global__ void bone_box_finish_kernel(const int *__restrict__ ibox, float *__restrict__ box) {
+  const int c = threadIdx.x;
+  if (c >= kBones) return;
+  const int *b = ibox + 6 * c;
+  const bool empty = b[0] > b[3];
+  for (int k = 0; k < 3; ++k) {
+    box[6 * c + k] = empty ? INFINITY : (float)(b[k] - 1);
+    box[6 * c + 3 + k] = empty ? -INFINITY : (float)(b[3 + k] + 1);
+  }
 }
 
 // --------------------------------------------------------- derived layouts
@@ -393,7 +456,11 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   // half-precision hash table, corner-block weight volume
   table_to_f16_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->table), s->n_table / 2, s->table16);
   build_quad_kernel<<<2048, 256, 0, st>>>(s->wvol, (int)s->wres, s->wquad);
-  launched += 1;
+  bone_box_init_kernel<<<1, kBones * 6, 0, st>>>(s->bone_ibox, (int)s->wres);
+  bone_box_kernel<<<nblk((long)kBones * s->wres * s->wres * s->wres, 256), 256, 0, st>>>(s->wvol, (int)s->wres,
+                                                                                        s->bone_ibox);
+  bone_box_finish_kernel<<<1, 32, 0, st>>>(s->bone_ibox, s->bone_box);
+  launched += 4;
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(launched + 1);
   s->params_dirty = false;
@@ -523,6 +590,7 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   P.tlay = s->tlay;
   P.G = s->d_G;
   P.bias1 = s->d_bias1;
+  P.bone_box = (o && !(o->flags & NR_RENDER_ALL_BONES)) ? s->bone_box : nullptr;
   P.fp8_blob = s->fp8_blob;
   P.fp8_scales = s->fp8_scales;
   P.t5_bf16 = s->t5_bf16;
@@ -550,7 +618,8 @@ static void free_subject(nr_subject *s) {
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
                   s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
                   s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG, s->f_omega_o,
-                  s->cnn, s->g_cnn, s->cnn_m, s->cnn_v, s->cnn_z, s->cnn_prior, s->cnn_act, s->cnn_grad};
+                  s->cnn, s->g_cnn, s->cnn_m, s->cnn_v, s->cnn_z, s->cnn_prior, s->cnn_act, s->cnn_grad,
+                  s->bone_box, s->bone_ibox};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
@@ -640,6 +709,8 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->table16, s->n_table * 2);
   ALLOC(s->blob, (size_t)s->lay.total * 4);
   ALLOC(s->wquad, quad_channel((int)s->wres) * kBones * sizeof(float4));
+  ALLOC(s->bone_box, kBones * 6 * sizeof(float));
+  ALLOC(s->bone_ibox, kBones * 6 * sizeof(int));
   ALLOC(s->tc_bf16, (size_t)s->tlay.total * 2);
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
   ALLOC(s->d_G, kBones * 12 * 4);

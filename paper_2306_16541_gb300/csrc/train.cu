@@ -748,6 +748,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   o.feat_dtype = NR_F32;
   o.hann_alpha = b->hann_alpha;
   FieldParams P = field_params(s, &o);
+  P.bone_box = nullptr;   // training differentiates every bone channel
   const size_t n = (size_t)b->n_rays * b->n_samples;
   const int blocks = num_sms(s->device);
   const int A = s->lay.total + (int)s->n_frames * kWidth;

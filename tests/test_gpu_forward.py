@@ -339,3 +339,22 @@ def test_round_based_termination_saves_work_and_matches_single_pass(tiny_structu
         S.close()
     assert live_on < 0.4 * live_off, (live_on, live_off)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("mlp", ["f32", "bf16"])
+def test_bone_skipping_changes_nothing_visible(mlp):
+    """Rendering skips bone channels whose support box misses the candidate point (their
+    weights are <= 1e-7 there); against evaluating all 24 channels the image moves by no
+    more than those weights can move it."""
+    nr = nrmod()
+    cfg = synth.config_frame512(structured=True)
+    cam = synth.camera(96, 96, 120.0, (0.0, 0.0, 2.5), 64, 0.5, 4.5)
+    S = nr.Subject(cfg["subject"])
+    try:
+        S.set_pose(*cfg["pose"])
+        skip = S.render(cam, nr.make_opts(mlp, "f16", True, 1e-4)).cpu().numpy()
+        full = S.render(cam, nr.make_opts(mlp, "f16", True, 1e-4, all_bones=True)).cpu().numpy()
+    finally:
+        S.close()
+    assert full[..., 3].max() > 0.2
+    assert np.abs(skip - full).max() <= 1e-4, np.abs(skip - full).max()
