@@ -52,7 +52,7 @@ def parse():
                    help="uniform random pixels, or 6 patches of 20x20 per image with MSE weight 0.2")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
     p.add_argument("--serve-only", action="store_true", help="run only the serving scenario")
-    p.add_argument("--serve-slots", type=int, default=4, help="concurrent requests on the device (server slots)")
+    p.add_argument("--serve-slots", type=int, default=8, help="concurrent requests on the device (server slots)")
     p.add_argument("--no-sweep", dest="sweep", action="store_false", help="skip the precision sweep")
     p.add_argument("--sweep-only", action="store_true", help="run only the precision sweep")
     return p.parse_args()

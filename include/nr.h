@@ -329,7 +329,10 @@ typedef struct {
 
 /* Creates a server on `device` with a device-memory budget for its slots
  * (each slot needs about 136 MiB) and a slot limit (1..256); starts its
- * worker thread.  NR_EINVAL if max_bytes cannot hold one slot. */
+ * worker thread.  Queued requests are dispatched smallest first (width x
+ * height x n_samples), except that a request queued for 40 ms or more goes
+ * first; requests of at most 512 x 512 pixels run on high-priority streams.
+ * NR_EINVAL if max_bytes cannot hold one slot. */
 nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t max_slots, nr_server **out);
 /* Registers a subject (not owned; it must outlive the server and must not be
  * trained or given new parameters while the server runs).  All subjects must

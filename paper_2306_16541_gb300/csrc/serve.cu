@@ -7,8 +7,11 @@
 //     derived layouts stay resident on the device;
 //   * a request (subject, camera, pose, options, output buffer) is queued by
 //     nr_server_submit from any host thread;
-//   * one worker thread admits queued requests in arrival order into slots.  A
-//     slot owns a CUDA stream, the request's pose buffers (bone transforms,
+//   * one worker thread admits queued requests into slots, smallest first (fewest
+//     pixel x sample slots; a request queued longer than kAgeMs goes first, in
+//     arrival order), so that short frames are not stuck behind long ones.  A
+//     slot owns two CUDA streams (high priority for requests of at most
+//     kSmallPixels pixels, low priority for the rest), the request's pose buffers (bone transforms,
 //     folded residual bias, posed occupancy bitfield) and its sample queues.
 //     Slots are created on demand while the device-memory budget allows and are
 //     reused afterwards: admission is by memory and by slot count;
@@ -37,10 +40,14 @@ using Clock = std::chrono::steady_clock;
 
 constexpr size_t kSlotSamples = size_t(1) << 22;   // sample-queue entries per slot
 constexpr size_t kSlotRays = size_t(1) << 17;      // rays per chunk at most
+constexpr double kAgeMs = 40.0;                      // a request queued this long is dispatched first
+constexpr uint64_t kSmallPixels = 512 * 512;         // requests up to this size run on high-priority streams
 
 struct Slot {
   int index = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // high priority: small requests
+  cudaStream_t stream_lo = nullptr;  // low priority: large requests
+  cudaStream_t cur = nullptr;        // the stream of the request in flight
   float *d_G = nullptr, *d_omega = nullptr, *d_bias1 = nullptr;
   uint32_t *bits = nullptr;
   FrameWork w{};
@@ -98,12 +105,14 @@ static size_t slot_bytes(int grid) {
 static void free_slot(Slot *sl) {
   if (!sl) return;
   if (sl->stream) cudaStreamSynchronize(sl->stream);
+  if (sl->stream_lo) cudaStreamSynchronize(sl->stream_lo);
   void *bufs[] = {sl->d_G,       sl->d_omega,   sl->d_bias1,      sl->bits,   sl->w.samp,
                   sl->w.samp_out, sl->w.ray_range, sl->w.counter, sl->w.state, sl->w.next};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (sl->h_pose) cudaFreeHost(sl->h_pose);
   if (sl->stream) cudaStreamDestroy(sl->stream);
+  if (sl->stream_lo) cudaStreamDestroy(sl->stream_lo);
   delete sl;
 }
 
@@ -118,7 +127,12 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
 #define SLOT_ALLOC(p, n)                                   \
   if ((e = cudaMalloc((void **)&(p), (n))) != cudaSuccess) \
     return fail(e, "slot allocation " #p);
-  if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+  int least = 0, greatest = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return fail(e, "stream priorities");
+  if ((e = cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
+    return fail(e, "stream");
+  if ((e = cudaStreamCreateWithPriority(&sl->stream_lo, cudaStreamNonBlocking, least)) != cudaSuccess)
+    return fail(e, "stream");
   SLOT_ALLOC(sl->d_G, kBones * 12 * sizeof(float));
   SLOT_ALLOC(sl->d_omega, (2 * kBones * 3 + 3) * sizeof(float));
   SLOT_ALLOC(sl->d_bias1, kWidth * sizeof(float));
@@ -165,7 +179,7 @@ static void CUDART_CB on_request_done(void *p) {
 static nr_status launch_request(nr_server *srv, Slot *sl, Request &q, DoneCtx *ctx) {
   const nr_request &r = q.r;
   nr_subject *s = srv->subjects[r.subject];
-  cudaStream_t st = sl->stream;
+  cudaStream_t st = sl->cur;
   memcpy(sl->h_pose + kBones * 12, r.axis_angle, sizeof(float) * kBones * 3);
   memcpy(sl->h_pose + kBones * 15, r.root_t, sizeof(float) * 3);
   NR_CHECK_CUDA(cudaMemcpyAsync(sl->d_omega, sl->h_pose + kBones * 12, sizeof(float) * (kBones * 3 + 3),
@@ -223,9 +237,25 @@ static void worker_main(nr_server *srv) {
       }
     }
     if (slot) {
-      const uint64_t id = srv->queue.front();
-      srv->queue.pop_front();
+      // smallest first, unless the oldest request has waited kAgeMs
+      auto pick = srv->queue.begin();
+      const double oldest_ms =
+          std::chrono::duration<double, std::milli>(Clock::now() - srv->reqs[*pick].t_submit).count();
+      if (oldest_ms < kAgeMs) {
+        uint64_t best = UINT64_MAX;
+        for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it) {
+          const nr_camera &c = srv->reqs[*it].r.cam;
+          const uint64_t work = (uint64_t)c.width * c.height * c.n_samples;
+          if (work < best) {
+            best = work;
+            pick = it;
+          }
+        }
+      }
+      const uint64_t id = *pick;
+      srv->queue.erase(pick);
       Request &q = srv->reqs[id];
+      slot->cur = (uint64_t)q.r.cam.width * q.r.cam.height <= kSmallPixels ? slot->stream : slot->stream_lo;
       q.state = 1;
       slot->busy = true;
       slot->req = id;
@@ -239,7 +269,7 @@ static void worker_main(nr_server *srv) {
       if (rc != NR_OK) {
         // nothing (or only part of the work) reached the stream: wait for it, then fail the request
         lock.unlock();
-        cudaStreamSynchronize(slot->stream);
+        cudaStreamSynchronize(slot->cur);
         lock.lock();
         Request &qq = srv->reqs[id];
         qq.state = -1;
