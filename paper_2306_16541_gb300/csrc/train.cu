@@ -23,7 +23,7 @@
 
 namespace nr {
 
-constexpr int kBwdThreads = 128;
+constexpr int kBwdThreads = 256;
 
 // Rows of a thread's scratch column (sized for the subject's hidden depth H).
 struct Rows {
@@ -329,11 +329,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     bool active = j < n && T.raycnt[r] != 0;
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active) g4 = T.out[j];
+    if (active) g4 = __ldcs(T.out + j);
     if (active) {
       // ---------------- forward recompute
       const float *G = T.fG + (size_t)f * kBones * 12;
-      const float4 s = T.samp[j];
+      const float4 s = __ldcs(T.samp + j);
       float xs0, xs1, xs2, S;
       lbs_warp(P, G, s.x, s.y, s.z, xs0, xs1, xs2, S);
       float xf0 = xs0, xf1 = xs1, xf2 = xs2;
