@@ -228,43 +228,90 @@ __device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const f
   }
 }
 
-// Warp-level weight gradient of one layer with 64 outputs: acc[wt + k*64 + j] += sum_s h[s][k] d[s][j],
-// added with fire-and-forget atomics into the block's accumulator (shared by its warps),
-// acc[b + j] += sum_s d[s][j]; lane owns j = lane and lane + 32.  `wcol` points at the warp's
-// column 0 (so row r of sample s is wcol[r * stride + s]).
+// TF32 with an error term: x = hi + lo, both exactly representable in tf32; a product
+// x y = hi_x hi_y + hi_x lo_y + lo_x hi_y up to a term below float32's rounding, so three
+// tensor-core products keep float32 accuracy ("3xTF32").
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Warp-level weight gradient of one layer with 64 outputs over the warp's 32 samples,
+// dW[j][k] = sum_s d[s][j] h[s][k], as the product D^T H on the tensor cores
+// (m16n8k8 TF32 MMAs, three per step for float32 accuracy): M = the 64 outputs in four
+// 16-row tiles, K = the 32 samples in four steps of 8, N = the inputs in tiles of 8.  Each
+// finished 16 x 8 tile is added into the block's accumulator acc[wt + k * 64 + j] with
+// fire-and-forget atomics (shared by the block's warps); acc[b + j] += sum_s d[s][j].
+// `wcol` points at the warp's column 0 (row r of sample s is wcol[r * stride + s]).
 __device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in, int n_in, int r_d, float *acc,
                                         int wt, int b, bool with_bias) {
-  const int lane = threadIdx.x & 31;
-  float d0[32], d1[32];
-  const float4 *p0 = reinterpret_cast<const float4 *>(wcol + (r_d + lane) * stride);
-  const float4 *p1 = reinterpret_cast<const float4 *>(wcol + (r_d + lane + 32) * stride);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 a = p0[q], c = p1[q];
-    d0[4 * q] = a.x; d0[4 * q + 1] = a.y; d0[4 * q + 2] = a.z; d0[4 * q + 3] = a.w;
-    d1[4 * q] = c.x; d1[4 * q + 1] = c.y; d1[4 * q + 2] = c.z; d1[4 * q + 3] = c.w;
-  }
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   if (with_bias) {
+    const float4 *p0 = reinterpret_cast<const float4 *>(wcol + (r_d + lane) * stride);
+    const float4 *p1 = reinterpret_cast<const float4 *>(wcol + (r_d + lane + 32) * stride);
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-      s0 += d0[s];
-      s1 += d1[s];
+    for (int q = 0; q < 8; ++q) {
+      const float4 a = p0[q], c = p1[q];
+      s0 += (a.x + a.y) + (a.z + a.w);
+      s1 += (c.x + c.y) + (c.z + c.w);
     }
     atomicAdd(acc + b + lane, s0);
     atomicAdd(acc + b + lane + 32, s1);
   }
-  for (int k = 0; k < n_in; ++k) {
-    const float4 *ph = reinterpret_cast<const float4 *>(wcol + (r_in + k) * stride);
-    float a0 = 0.f, a1 = 0.f;
+  // A = D^T fragments of all four row tiles, one per step of 8 samples: loaded once per layer
+  uint32_t ah[4][4][4], al[4][4][4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 h = ph[q];
-      a0 = fmaf(h.x, d0[4 * q], fmaf(h.y, d0[4 * q + 1], fmaf(h.z, d0[4 * q + 2], fmaf(h.w, d0[4 * q + 3], a0))));
-      a1 = fmaf(h.x, d1[4 * q], fmaf(h.y, d1[4 * q + 1], fmaf(h.z, d1[4 * q + 2], fmaf(h.w, d1[4 * q + 3], a1))));
+  for (int m = 0; m < 4; ++m) {
+    const float *d0 = wcol + (r_d + 16 * m + g) * stride;
+    const float *d8 = d0 + 8 * stride;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int s = 8 * ks + t;
+      tf32_split(d0[s], ah[m][ks][0], al[m][ks][0]);
+      tf32_split(d8[s], ah[m][ks][1], al[m][ks][1]);
+      tf32_split(d0[s + 4], ah[m][ks][2], al[m][ks][2]);
+      tf32_split(d8[s + 4], ah[m][ks][3], al[m][ks][3]);
     }
-    atomicAdd(acc + wt + k * kWidth + lane, a0);
-    atomicAdd(acc + wt + k * kWidth + lane + 32, a1);
+  }
+#pragma unroll 1
+  for (int n0 = 0; n0 < n_in; n0 += 8) {
+    uint32_t bh[4][2], bl[4][2];   // B = H fragments of this column tile
+    const float *hk = wcol + (r_in + n0 + g) * stride;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      tf32_split(hk[8 * ks + t], bh[ks][0], bl[ks][0]);
+      tf32_split(hk[8 * ks + t + 4], bh[ks][1], bl[ks][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        mma_tf32(c, al[m][ks], bh[ks]);
+        mma_tf32(c, ah[m][ks], bl[ks]);
+        mma_tf32(c, ah[m][ks], bh[ks]);
+      }
+      // c = C[16m + g][n0 + 2t], C[16m + g][n0 + 2t + 1], C[16m + g + 8][n0 + 2t], C[16m + g + 8][n0 + 2t + 1]
+      float *o = acc + wt + (n0 + 2 * t) * kWidth + 16 * m + g;
+      atomicAdd(o, c[0]);
+      atomicAdd(o + kWidth, c[1]);
+      atomicAdd(o + 8, c[2]);
+      atomicAdd(o + kWidth + 8, c[3]);
+    }
   }
 }
 
