@@ -240,6 +240,7 @@ nr_status nr_set_frames(nr_subject *s, uint32_t n_frames, const float *axis_angl
                         const float *root_t, const nr_camera *cams, void *stream);
 
 #define NR_GRAD_ONLY 1u        /* compute gradients into the grad buffers, skip Adam */
+#define NR_FORWARD_ONLY 2u     /* composite the batch (into pred_rgb) and stop: no gradient, no Adam */
 
 #define NR_TRAIN_WVOL 1u
 #define NR_TRAIN_HASH 2u
@@ -263,7 +264,7 @@ typedef struct {
   uint64_t step_seed;
   float lr, beta1, beta2, eps;   /* Adam (Sec. 5.2: beta = (0.9, 0.99)) */
   float hann_alpha;              /* residual PE window; < 0 = all bands */
-  uint32_t flags;                /* NR_GRAD_ONLY */
+  uint32_t flags;                /* NR_GRAD_ONLY, NR_FORWARD_ONLY */
   uint32_t train_mask;           /* NR_TRAIN_* groups that are updated; 0 = all */
   float lr_scale[4];             /* per-group multiplier of lr: weight volume, hash table,
                                     canonical MLP, residual MLP; 0 means 1.  Sec. 5.2 trains
@@ -272,6 +273,11 @@ typedef struct {
                                     LPIPS); 0 means 1 */
   float lr_scale_refiner;        /* lr multiplier of the pose refiner; 0 means 1 */
   float lr_scale_cnn;            /* lr multiplier of the weight-volume generator; 0 means 1 */
+  float *pred_rgb;               /* optional device float32[n][3]: receives each ray's colour
+                                    C^ + T_final bg */
+  const float *grad_rgb;         /* optional device float32[n][3]: dL/dC^ of each ray from the
+                                    caller's own loss; replaces the MSE and its gradient
+                                    (target_rgb is then not read and *loss_out is 0) */
 } nr_train_batch;
 
 /* Forward, loss L = loss_weight * mean over rays and channels of (C^ - C_gt)^2, the

@@ -80,6 +80,9 @@ struct TrainDev {
   Rows rw;
   float *dG;              // [F][24][12] dL/dG of every frame (pose refiner), or NULL
   int dG_smem;            // 1: the block sums dG in shared memory first
+  float *pred;            // [n][3] composited colours out, or NULL
+  const float *grad_rgb;  // [n][3] dL/dC from the caller, or NULL (MSE against target)
+  int forward_only;       // stop after compositing
 };
 
 // ----------------------------------------------------------------- rays
@@ -187,12 +190,26 @@ __global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
       Tr *= 1.f - v.w;
     }
     const float C0 = fmaf(Tr, T.bg[0], c0), C1 = fmaf(Tr, T.bg[1], c1), C2 = fmaf(Tr, T.bg[2], c2);
-    const float e0 = C0 - T.target[3 * r], e1 = C1 - T.target[3 * r + 1], e2 = C2 - T.target[3 * r + 2];
-    lsum = T.loss_weight * (e0 * e0 + e1 * e1 + e2 * e2);
-    const float scale = 2.f * T.loss_weight / (3.f * (float)T.n_rays);
-    const float g0 = scale * e0, g1 = scale * e1, g2 = scale * e2;
+    if (T.pred) {
+      T.pred[3 * r] = C0;
+      T.pred[3 * r + 1] = C1;
+      T.pred[3 * r + 2] = C2;
+    }
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (T.grad_rgb) {   // the caller's dL/dC
+      g0 = T.grad_rgb[3 * r];
+      g1 = T.grad_rgb[3 * r + 1];
+      g2 = T.grad_rgb[3 * r + 2];
+    } else if (T.target) {
+      const float e0 = C0 - T.target[3 * r], e1 = C1 - T.target[3 * r + 1], e2 = C2 - T.target[3 * r + 2];
+      lsum = T.loss_weight * (e0 * e0 + e1 * e1 + e2 * e2);
+      const float scale = 2.f * T.loss_weight / (3.f * (float)T.n_rays);
+      g0 = scale * e0;
+      g1 = scale * e1;
+      g2 = scale * e2;
+    }
     float B = T.bg[0] * g0 + T.bg[1] * g1 + T.bg[2] * g2;
-    for (int i = (int)cnt - 1; i >= 0; --i) {
+    for (int i = T.forward_only ? -1 : (int)cnt - 1; i >= 0; --i) {
       const float4 v = T.out[base + i];
       const float Ti = T.T[base + i];
       const float cg = v.x * g0 + v.y * g1 + v.z * g2;
@@ -761,7 +778,9 @@ using namespace nr;
 extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float *loss_out, void *stream) {
   NR_REQUIRE(subject_ok(s), "nr_train_step: invalid handle");
   NR_REQUIRE(b, "nr_train_step: NULL batch");
-  NR_REQUIRE(b->n_rays >= 1 && b->frame_id && b->px && b->py && b->target_rgb, "nr_train_step: empty or NULL batch");
+  NR_REQUIRE(b->n_rays >= 1 && b->frame_id && b->px && b->py, "nr_train_step: empty or NULL batch");
+  const bool fwd_only = (b->flags & NR_FORWARD_ONLY) != 0;
+  NR_REQUIRE(b->target_rgb || b->grad_rgb || fwd_only, "nr_train_step: neither target_rgb nor grad_rgb");
   NR_REQUIRE(b->n_samples >= 1 && b->n_samples <= 1024, "nr_train_step: n_samples must be 1..1024");
   NR_REQUIRE((uint64_t)b->n_rays * b->n_samples <= (1ull << 31), "nr_train_step: batch too large");
   NR_REQUIRE(b->lr >= 0.f && b->beta1 >= 0.f && b->beta1 < 1.f && b->beta2 >= 0.f && b->beta2 < 1.f && b->eps > 0.f,
@@ -868,6 +887,9 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.rw = rows;
   T.dG = refine ? s->f_dG : nullptr;
   T.dG_smem = dG_smem ? 1 : 0;
+  T.pred = b->pred_rgb;
+  T.grad_rgb = fwd_only ? nullptr : b->grad_rgb;
+  T.forward_only = fwd_only ? 1 : 0;
 
   train_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
                                                                      s->bmax[1], s->bmax[2]);
@@ -878,6 +900,14 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_CHECK_CUDA(cudaGetLastError());
   train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
   NR_CHECK_CUDA(cudaGetLastError());
+  if (fwd_only) {
+    count_launches(launched + 4);
+    if (loss_out) {
+      NR_CHECK_CUDA(cudaMemcpyAsync(loss_out, s->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st));
+      NR_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    return NR_OK;
+  }
   const size_t smem_b = sizeof(float) * (s->lay.total + (dG_smem ? n_dG : 0));
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);

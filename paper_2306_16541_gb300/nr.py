@@ -22,6 +22,7 @@ NR_F32, NR_F16, NR_BF16, NR_FP8E4M3 = range(4)
 DTYPES = {"f32": NR_F32, "f16": NR_F16, "bf16": NR_BF16, "fp8": NR_FP8E4M3}
 NR_POSE_MATRICES = 1
 NR_GRAD_ONLY = 1
+NR_FORWARD_ONLY = 2
 NR_TRAIN_WVOL, NR_TRAIN_HASH, NR_TRAIN_MLP, NR_TRAIN_RES, NR_TRAIN_REFINER, NR_TRAIN_CNN = 1, 2, 4, 8, 16, 32
 NR_TRAIN_ALL = 63
 NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES, NR_PARAM_REFINER, NR_PARAM_CNN = range(6)
@@ -72,7 +73,8 @@ class nr_train_batch(C.Structure):
                 ("step_seed", C.c_uint64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("hann_alpha", C.c_float), ("flags", C.c_uint32),
                 ("train_mask", C.c_uint32), ("lr_scale", C.c_float * 4), ("loss_weight", C.c_float),
-                ("lr_scale_refiner", C.c_float), ("lr_scale_cnn", C.c_float)]
+                ("lr_scale_refiner", C.c_float), ("lr_scale_cnn", C.c_float),
+                ("pred_rgb", _fp), ("grad_rgb", _fp)]
 
 
 class nr_request(C.Structure):
@@ -278,6 +280,8 @@ def nr_param(h, which: int):
     import torch
     p, g, n = C.c_void_p(), C.c_void_p(), C.c_size_t()
     check(lib.nr_param(h, which, C.byref(p), C.byref(g), C.byref(n)), "nr_param")
+    if n.value == 0 or not p.value:   # a group not in use (no refiner, no CNN_skel)
+        return (torch.empty(0, device="cuda"), torch.empty(0, device="cuda"))
     return (torch.as_tensor(_DevArray(p.value, n.value), device="cuda"),
             torch.as_tensor(_DevArray(g.value, n.value), device="cuda"))
 
@@ -379,17 +383,23 @@ class Subject:
                    betas=(0.9, 0.99), eps: float = 1e-8, bg=(0.0, 0.0, 0.0), hann_alpha: float = -1.0,
                    grad_only: bool = False, train_mask: int = 0, lr_scale=(0.0, 0.0, 0.0, 0.0),
                    loss_weight: float = 0.0, lr_scale_refiner: float = 0.0, lr_scale_cnn: float = 0.0,
-                   stream=None) -> float:
+                   pred_rgb=None, grad_rgb=None, forward_only: bool = False, stream=None) -> float:
         b = nr_train_batch()
         b.n_rays = int(frame_id.shape[0])
         b.frame_id = C.cast(C.c_void_p(frame_id.data_ptr()), _up)
         b.px = C.cast(C.c_void_p(px.data_ptr()), _up)
         b.py = C.cast(C.c_void_p(py.data_ptr()), _up)
-        b.target_rgb = C.cast(C.c_void_p(target_rgb.data_ptr()), _fp)
+        if target_rgb is not None:
+            b.target_rgb = C.cast(C.c_void_p(target_rgb.data_ptr()), _fp)
+        if pred_rgb is not None:
+            b.pred_rgb = C.cast(C.c_void_p(pred_rgb.data_ptr()), _fp)
+        if grad_rgb is not None:
+            b.grad_rgb = C.cast(C.c_void_p(grad_rgb.data_ptr()), _fp)
         b.n_samples, b.step_seed = int(n_samples), int(step_seed)
         b.bg[:] = [float(v) for v in bg]
         b.lr, b.beta1, b.beta2, b.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
-        b.hann_alpha, b.flags, b.train_mask = float(hann_alpha), NR_GRAD_ONLY if grad_only else 0, int(train_mask)
+        b.hann_alpha, b.train_mask = float(hann_alpha), int(train_mask)
+        b.flags = (NR_GRAD_ONLY if grad_only else 0) | (NR_FORWARD_ONLY if forward_only else 0)
         b.lr_scale[:] = [float(v) for v in lr_scale]
         b.loss_weight = float(loss_weight)
         b.lr_scale_refiner = float(lr_scale_refiner)
@@ -398,6 +408,24 @@ class Subject:
 
     def param(self, which: int):
         return nr_param(self.h, which)
+
+    def parameter_groups(self):
+        """The trainable groups in use: weight volume (or CNN_skel), hash table, canonical
+        MLP, residual MLP, and the pose refiner when one is installed."""
+        groups = [NR_PARAM_WVOL, NR_PARAM_HASH, NR_PARAM_MLP, NR_PARAM_RES]
+        if self.param(NR_PARAM_REFINER)[0].numel():
+            groups.append(NR_PARAM_REFINER)
+        if self.param(NR_PARAM_CNN)[0].numel():
+            groups[0] = NR_PARAM_CNN
+        return groups
+
+    def parameters(self):
+        """Zero-copy device tensors of the groups in use, marked requires_grad (leaf tensors
+        for torch.autograd and torch.optim)."""
+        return [self.param(g)[0].requires_grad_(True) for g in self.parameter_groups()]
+
+    def parameter_grads(self):
+        return [self.param(g)[1] for g in self.parameter_groups()]
 
     def params_changed(self):
         nr_params_changed(self.h)
@@ -436,6 +464,48 @@ class Subject:
             self.close()
         except Exception:
             pass
+
+
+class RenderFn:
+    """The training render as a torch.autograd.Function: colours of a batch of pixel rays
+    (stratified samples, as in nr_train_step), differentiable in the subject's parameter
+    groups through the library's hand-written backward.
+
+        params = sub.parameters()               # zero-copy device tensors, requires_grad
+        rgb = RenderFn.apply(sub, frame_id, px, py, n_samples, seed, *params)
+        loss = any_function(rgb); loss.backward()    # params[i].grad filled by the library
+        optimizer.step(); sub.params_changed()       # the library rebuilds its derived layouts
+
+    The backward re-runs the batch's forward (same seed, so the same samples) and feeds
+    dL/drgb into the compositing adjoint."""
+
+    @staticmethod
+    def apply(sub, frame_id, px, py, n_samples, seed, *params):
+        return _render_fn().apply(sub, frame_id, px, py, n_samples, seed, *params)
+
+
+def _render_fn():
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, sub, frame_id, px, py, n_samples, seed, *params):
+            pred = torch.empty(frame_id.shape[0], 3, device=frame_id.device, dtype=torch.float32)
+            sub.train_step(frame_id, px, py, None, int(n_samples), int(seed), pred_rgb=pred, forward_only=True)
+            ctx.sub, ctx.n_samples, ctx.seed, ctx.n_params = sub, int(n_samples), int(seed), len(params)
+            ctx.save_for_backward(frame_id, px, py)
+            return pred
+
+        @staticmethod
+        def backward(ctx, grad_pred):
+            frame_id, px, py = ctx.saved_tensors
+            sub = ctx.sub
+            sub.train_step(frame_id, px, py, None, ctx.n_samples, ctx.seed,
+                           grad_rgb=grad_pred.contiguous().float(), grad_only=True)
+            grads = [g.clone() for g in sub.parameter_grads()[:ctx.n_params]]
+            return (None, None, None, None, None, None) + tuple(grads)
+
+    return _Fn
 
 
 class Server:
