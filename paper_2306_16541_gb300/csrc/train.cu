@@ -59,6 +59,57 @@ static Rows make_rows(int H) {
   return r;
 }
 
+// The backward kernel's shared-memory copy of the float32 blob: each layer [in][out] with the
+// rows of 64-output layers padded to kPadRow floats, so that the tensor-core fragments of
+// W^T (8 rows x 4 columns per load) fall in distinct banks.
+constexpr int kPadRow = 68;
+constexpr int kMaxSeg = 2 * (6 + kMaxHidden);
+struct PadSeg {
+  int src, dst, rows, cols, dstride;
+};
+struct PadLay {
+  int r1, r2, r3, r4, r5, c0, ch[kMaxHidden], cl;
+  int r1b, r2b, r3b, r4b, r5b, c0b, chb[kMaxHidden], clb;
+  int n_seg;
+  PadSeg seg[kMaxSeg];
+  int total;   // floats
+};
+
+static PadLay pad_layout(const BlobLayout &b, int H) {
+  PadLay p{};
+  int o = 0;
+  auto add = [&](int src, int rows, int cols) {
+    PadSeg &g = p.seg[p.n_seg++];
+    g.src = src;
+    g.dst = o;
+    g.rows = rows;
+    g.cols = cols;
+    g.dstride = cols == kWidth ? kPadRow : cols;
+    o += (rows * g.dstride + 3) & ~3;
+    return g.dst;
+  };
+  p.r1 = add(b.r1, kResGammaPad, kWidth);
+  p.r1b = add(b.r1b, 1, kWidth);
+  p.r2 = add(b.r2, kWidth, kWidth);
+  p.r2b = add(b.r2b, 1, kWidth);
+  p.r3 = add(b.r3, kWidth, kWidth);
+  p.r3b = add(b.r3b, 1, kWidth);
+  p.r4 = add(b.r4, kWidth + kResGammaPad, kWidth);
+  p.r4b = add(b.r4b, 1, kWidth);
+  p.r5 = add(b.r5, kWidth, 4);
+  p.r5b = add(b.r5b, 1, 4);
+  p.c0 = add(b.c0, kMlpIn, kWidth);
+  p.c0b = add(b.c0b, 1, kWidth);
+  for (int l = 0; l < H - 1; ++l) {
+    p.ch[l] = add(b.ch[l], kWidth, kWidth);
+    p.chb[l] = add(b.chb[l], 1, kWidth);
+  }
+  p.cl = add(b.cl, kWidth, 4);
+  p.clb = add(b.clb, 1, 4);
+  p.total = o;
+  return p;
+}
+
 struct TrainDev {
   const uint32_t *frame_id, *px, *py;
   const float *target;
@@ -80,6 +131,7 @@ struct TrainDev {
   Rows rw;
   float *dG;              // [F][24][12] dL/dG of every frame (pose refiner), or NULL
   int dG_smem;            // 1: the block sums dG in shared memory first
+  PadLay pl;              // shared-memory layout of the backward kernel's weights
   float *pred;            // [n][3] composited colours out, or NULL
   const float *grad_rgb;  // [n][3] dL/dC from the caller, or NULL (MSE against target)
   int forward_only;       // stop after compositing
@@ -361,18 +413,110 @@ __device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, 
   }
 }
 
+// y = W x + b over the padded copy (row k of W^T at Wt + k * rs), x in the thread's column.
+template <int OUT>
+__device__ __forceinline__ void dense_rs(const float *__restrict__ Wt, int rs, const float *__restrict__ b,
+                                         const float *__restrict__ col, int in, int stride, float (&y)[OUT],
+                                         bool init = true) {
+  if (init) {
+#pragma unroll
+    for (int j = 0; j < OUT; ++j) y[j] = b[j];
+  }
+#pragma unroll 2
+  for (int k = 0; k < in; ++k) {
+    const float xk = col[k * stride];
+    const float4 *row = reinterpret_cast<const float4 *>(Wt + k * rs);
+#pragma unroll
+    for (int j = 0; j < OUT / 4; ++j) {
+      const float4 w = row[j];
+      y[4 * j + 0] = fmaf(xk, w.x, y[4 * j + 0]);
+      y[4 * j + 1] = fmaf(xk, w.y, y[4 * j + 1]);
+      y[4 * j + 2] = fmaf(xk, w.z, y[4 * j + 2]);
+      y[4 * j + 3] = fmaf(xk, w.w, y[4 * j + 3]);
+    }
+  }
+}
+
+// The backward of one layer for the warp's 32 samples on the tensor cores:
+//   out[s][i] = (sum_o W^T[i][o] delta[s][o]) * (h[s][i] > 0)     (no mask when r_h < 0)
+// as C = W^T D^T with M = IN (16-row tiles of inputs), N = the 32 samples (4 tiles of 8),
+// K = OUT (steps of 8; a 4-output layer pads its step with zeros); m16n8k8 TF32 MMAs, three
+// per step for float32 accuracy.  W^T comes from the padded shared copy (row i at Wt + i * rs),
+// delta from scratch rows r_d.., the mask from rows r_h..; the result goes to rows r_out..
+// (added to them when `accumulate`).  Every lane of the warp must take part.
+template <int OUT, int IN>
+__device__ __forceinline__ void warp_back(const float *__restrict__ Wt, int rs, float *wcol, int stride, int r_d,
+                                          int r_h, int r_out, bool accumulate) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  constexpr int KS = (OUT + 7) / 8, MT = IN / 16;
+  float acc[MT][4][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+#pragma unroll 1
+  for (int ks = 0; ks < KS; ++ks) {
+    const int o0 = 8 * ks + t, o1 = o0 + 4;
+    uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const float u0 = o0 < OUT ? wcol[(r_d + o0) * stride + 8 * n + g] : 0.f;
+      const float u1 = o1 < OUT ? wcol[(r_d + o1) * stride + 8 * n + g] : 0.f;
+      tf32_split(u0, bh[n][0], bl[n][0]);
+      tf32_split(u1, bh[n][1], bl[n][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const float *w0 = Wt + (16 * m + g) * rs, *w8 = w0 + 8 * rs;
+      uint32_t ah[4], al[4];
+      tf32_split(o0 < OUT ? w0[o0] : 0.f, ah[0], al[0]);
+      tf32_split(o0 < OUT ? w8[o0] : 0.f, ah[1], al[1]);
+      tf32_split(o1 < OUT ? w0[o1] : 0.f, ah[2], al[2]);
+      tf32_split(o1 < OUT ? w8[o1] : 0.f, ah[3], al[3]);
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        mma_tf32(acc[m][n], al, bh[n]);
+        mma_tf32(acc[m][n], ah, bl[n]);
+        mma_tf32(acc[m][n], ah, bh[n]);
+      }
+    }
+  }
+  // acc[m][n] = C[16m + g][8n + 2t], C[16m + g][8n + 2t + 1], C[16m + g + 8][8n + 2t], C[16m + g + 8][8n + 2t + 1]
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 16 * m + g + (q >= 2 ? 8 : 0), smp = 8 * n + 2 * t + (q & 1);
+        float v = acc[m][n][q];
+        if (r_h >= 0 && !(wcol[(r_h + i) * stride + smp] > 0.f)) v = 0.f;
+        float *dst = wcol + (r_out + i) * stride + smp;
+        *dst = accumulate ? *dst + v : v;
+      }
+  __syncwarp();   // the next layer reads these rows through other lanes
+}
+
 // One thread per sample: forward recompute (activations into the thread's scratch
 // column), backward, scatter-adds, then the warp's weight-gradient reduction.
 __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P, TrainDev T) {
   extern __shared__ float4 smem4[];
-  float *sW = reinterpret_cast<float *>(smem4);
-  float *sdG = sW + P.lay.total;                       // [F][24][12] when T.dG_smem
-  for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
-    reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
+  float *sW = reinterpret_cast<float *>(smem4);        // the weights in the padded layout T.pl
+  float *sdG = sW + T.pl.total;                        // [F][24][12] when T.dG_smem
+  for (int q = 0; q < T.pl.n_seg; ++q) {
+    const PadSeg &sg = T.pl.seg[q];
+    for (int i = threadIdx.x; i < sg.rows * sg.cols; i += blockDim.x) {
+      const int rr = i / sg.cols, cc = i - rr * sg.cols;
+      sW[sg.dst + rr * sg.dstride + cc] = __ldg(P.blob + sg.src + i);
+    }
+  }
   if (T.dG && T.dG_smem)
     for (int i = threadIdx.x; i < T.n_frames * kBones * 12; i += blockDim.x) sdG[i] = 0.f;
   __syncthreads();
-  const BlobLayout &Ly = P.lay;
+  const BlobLayout &Ly = P.lay;                        // the gradient accumulators' layout
+  const PadLay &PL = T.pl;
   const int stride = blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Rows &RW = T.rw;
@@ -380,7 +524,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
             R_DENC = RW.denc, R_DGAM = RW.dgam, R_DP = RW.dp, R_XS = RW.xs, kRows = RW.total;
   float *colbase = T.scratch + (size_t)blockIdx.x * kRows * stride;
   float *col = colbase + threadIdx.x;                  // this thread's column
-  const float *wcol = colbase + warp * 32;             // the warp's column 0
+  float *wcol = colbase + warp * 32;                   // the warp's column 0
   float *acc = T.wacc + (size_t)blockIdx.x * T.acc_floats;
   float *accF = acc + Ly.total;                        // per-frame first-layer bias gradients [F][64]
   const int H = P.hidden;
@@ -394,28 +538,33 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) g4 = __ldcs(T.out + j);
+    // per-sample state carried across the warp-level phases below
+    const float *G = T.fG + (size_t)f * kBones * 12;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float xs0 = 0.f, xs1 = 0.f, xs2 = 0.f, S = 0.f, xf0 = 0.f, xf1 = 0.f, xf2 = 0.f, dS_alpha = 0.f;
     if (active) {
-      // ---------------- forward recompute
-      const float *G = T.fG + (size_t)f * kBones * 12;
-      const float4 s = __ldcs(T.samp + j);
-      float xs0, xs1, xs2, S;
+      // ---------------- forward recompute (CUDA cores, one sample per thread)
+      s = __ldcs(T.samp + j);
       lbs_warp(P, G, s.x, s.y, s.z, xs0, xs1, xs2, S);
-      float xf0 = xs0, xf1 = xs1, xf2 = xs2;
+      xf0 = xs0;
+      xf1 = xs1;
+      xf2 = xs2;
       float y[kWidth];
       const float *bias1 = T.fbias1 + (size_t)f * kWidth;
       pos_enc(P, xs0, xs1, xs2, col + R_GAM * stride, stride);
       if (P.res_enabled) {
-        dense_f32<kWidth>(sW + Ly.r1, bias1, col + R_GAM * stride, kResGammaPad, stride, y);
+        dense_rs<kWidth>(sW + PL.r1, kPadRow, bias1, col + R_GAM * stride, kResGammaPad, stride, y);
         store_relu(y, col + (R_RH + 0 * kWidth) * stride, stride);
-        dense_f32<kWidth>(sW + Ly.r2, sW + Ly.r2b, col + (R_RH + 0 * kWidth) * stride, kWidth, stride, y);
+        dense_rs<kWidth>(sW + PL.r2, kPadRow, sW + PL.r2b, col + (R_RH + 0 * kWidth) * stride, kWidth, stride, y);
         store_relu(y, col + (R_RH + 1 * kWidth) * stride, stride);
-        dense_f32<kWidth>(sW + Ly.r3, sW + Ly.r3b, col + (R_RH + 1 * kWidth) * stride, kWidth, stride, y);
+        dense_rs<kWidth>(sW + PL.r3, kPadRow, sW + PL.r3b, col + (R_RH + 1 * kWidth) * stride, kWidth, stride, y);
         store_relu(y, col + (R_RH + 2 * kWidth) * stride, stride);
-        dense_f32<kWidth>(sW + Ly.r4, sW + Ly.r4b, col + (R_RH + 2 * kWidth) * stride, kWidth, stride, y);
-        dense_acc_f32<kWidth>(sW + Ly.r4 + kWidth * kWidth, col + R_GAM * stride, kResGammaPad, stride, y);
+        dense_rs<kWidth>(sW + PL.r4, kPadRow, sW + PL.r4b, col + (R_RH + 2 * kWidth) * stride, kWidth, stride, y);
+        dense_rs<kWidth>(sW + PL.r4 + kWidth * kPadRow, kPadRow, nullptr, col + R_GAM * stride, kResGammaPad, stride,
+                         y, false);
         store_relu(y, col + (R_RH + 3 * kWidth) * stride, stride);
         float o3[4];
-        dense_f32<4>(sW + Ly.r5, sW + Ly.r5b, col + (R_RH + 3 * kWidth) * stride, kWidth, stride, o3);
+        dense_rs<4>(sW + PL.r5, 4, sW + PL.r5b, col + (R_RH + 3 * kWidth) * stride, kWidth, stride, o3);
         xf0 += o3[0];
         xf1 += o3[1];
         xf2 += o3[2];
@@ -423,15 +572,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         for (int q = 0; q < 4 * kWidth; ++q) col[(R_RH + q) * stride] = 0.f;
       }
       const bool inside = hash_encode(P, xf0, xf1, xf2, col + R_ENC * stride, stride);
-      dense_f32<kWidth>(sW + Ly.c0, sW + Ly.c0b, col + R_ENC * stride, kMlpIn, stride, y);
+      dense_rs<kWidth>(sW + PL.c0, kPadRow, sW + PL.c0b, col + R_ENC * stride, kMlpIn, stride, y);
       store_relu(y, col + R_CH * stride, stride);
       for (int l = 1; l < H; ++l) {
-        dense_f32<kWidth>(sW + Ly.ch[l - 1], sW + Ly.chb[l - 1], col + (R_CH + (l - 1) * kWidth) * stride, kWidth,
-                          stride, y);
+        dense_rs<kWidth>(sW + PL.ch[l - 1], kPadRow, sW + PL.chb[l - 1], col + (R_CH + (l - 1) * kWidth) * stride,
+                         kWidth, stride, y);
         store_relu(y, col + (R_CH + l * kWidth) * stride, stride);
       }
       float o[4];
-      dense_f32<4>(sW + Ly.cl, sW + Ly.clb, col + (R_CH + (H - 1) * kWidth) * stride, kWidth, stride, o);
+      dense_rs<4>(sW + PL.cl, 4, sW + PL.clb, col + (R_CH + (H - 1) * kWidth) * stride, kWidth, stride, o);
       active = inside;
       if (active) {
         // ---------------- alpha, rgb, sigma
@@ -439,25 +588,31 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         const float e = expf(-sig * s.w);
         const float lk = fminf(S, 1.f);
         const float dsig = g4.w * s.w * e * lk;
-        const float dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
+        dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
         const float gc[3] = {g4.x, g4.y, g4.z};
-        float* dcl = col + (D_C + H * kWidth) * stride;
+        float *dcl = col + (D_C + H * kWidth) * stride;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const float c = sigmoidf_(o[k]);
           dcl[k * stride] = gc[k] * c * (1.f - c);
         }
         dcl[3 * stride] = dsig * sigmoidf_(o[3]);
-        // ---------------- canonical MLP backward
-        back_layer<4>(sW + Ly.cl, dcl, kWidth, col + (R_CH + (H - 1) * kWidth) * stride,
-                      col + (D_C + (H - 1) * kWidth) * stride, stride);
-        for (int l = H - 1; l >= 1; --l)
-          back_layer<kWidth>(sW + Ly.ch[l - 1], col + (D_C + l * kWidth) * stride, kWidth,
-                             col + (R_CH + (l - 1) * kWidth) * stride, col + (D_C + (l - 1) * kWidth) * stride,
-                             stride);
-        back_layer<kWidth>(sW + Ly.c0, col + D_C * stride, kMlpIn, nullptr, col + R_DENC * stride, stride);
-        // ---------------- hash backward: scatter-add and dL/dx_final
-        float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
+      }
+    }
+    if (!active)
+      for (int k = 0; k < 4; ++k) col[(D_C + H * kWidth + k) * stride] = 0.f;
+    __syncwarp();
+    // ---------------- canonical MLP backward: the warp's 32 samples on the tensor cores
+    warp_back<4, kWidth>(sW + PL.cl, 4, wcol, stride, D_C + H * kWidth, R_CH + (H - 1) * kWidth,
+                         D_C + (H - 1) * kWidth, false);
+    for (int l = H - 1; l >= 1; --l)
+      warp_back<kWidth, kWidth>(sW + PL.ch[l - 1], kPadRow, wcol, stride, D_C + l * kWidth, R_CH + (l - 1) * kWidth,
+                                D_C + (l - 1) * kWidth, false);
+    warp_back<kWidth, kMlpIn>(sW + PL.c0, kPadRow, wcol, stride, D_C, -1, R_DENC, false);
+    __syncwarp();
+    float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
+    if (active) {
+      // ---------------- hash backward: scatter-add and dL/dx_final
         {
           const float p0 = (xf0 - P.bmin[0]) * P.inv_box[0];
           const float p1 = (xf1 - P.bmin[1]) * P.inv_box[1];
@@ -494,39 +649,29 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           dx1 *= P.inv_box[1];
           dx2 *= P.inv_box[2];
         }
-        // ---------------- residual MLP backward (x_final = x_skel + x_res)
-        float ds0 = dx0, ds1 = dx1, ds2 = dx2;
-        if (P.res_enabled) {
-          float *dr5 = col + D_R5 * stride;
-          dr5[0] = dx0;
-          dr5[stride] = dx1;
-          dr5[2 * stride] = dx2;
-          dr5[3 * stride] = 0.f;
-          back_layer<4>(sW + Ly.r5, dr5, kWidth, col + (R_RH + 3 * kWidth) * stride, col + (D_R + 3 * kWidth) * stride,
-                        stride);
-          back_layer<kWidth>(sW + Ly.r4, col + (D_R + 3 * kWidth) * stride, kWidth, col + (R_RH + 2 * kWidth) * stride,
-                             col + (D_R + 2 * kWidth) * stride, stride);
-          back_layer<kWidth>(sW + Ly.r4 + kWidth * kWidth, col + (D_R + 3 * kWidth) * stride, kResGammaPad, nullptr,
-                             col + R_DGAM * stride, stride);
-          back_layer<kWidth>(sW + Ly.r3, col + (D_R + 2 * kWidth) * stride, kWidth, col + (R_RH + 1 * kWidth) * stride,
-                             col + (D_R + 1 * kWidth) * stride, stride);
-          back_layer<kWidth>(sW + Ly.r2, col + (D_R + 1 * kWidth) * stride, kWidth, col + (R_RH + 0 * kWidth) * stride,
-                             col + (D_R + 0 * kWidth) * stride, stride);
-          {  // dL/dgamma += W1_gamma^T delta1
-            float d[kWidth];
-#pragma unroll
-            for (int q = 0; q < kWidth; ++q) d[q] = col[(D_R + q) * stride];
-            for (int k = 0; k < kResGammaPad; ++k) {
-              const float4 *row = reinterpret_cast<const float4 *>(sW + Ly.r1 + k * kWidth);
-              float a = 0.f;
-#pragma unroll
-              for (int q = 0; q < kWidth / 4; ++q) {
-                const float4 w = row[q];
-                a = fmaf(w.x, d[4 * q], fmaf(w.y, d[4 * q + 1], fmaf(w.z, d[4 * q + 2], fmaf(w.w, d[4 * q + 3], a))));
-              }
-              col[(R_DGAM + k) * stride] += a;
-            }
-          }
+    }
+    float ds0 = dx0, ds1 = dx1, ds2 = dx2;
+    if (P.res_enabled) {
+      // ---------------- residual MLP backward (x_final = x_skel + x_res), tensor cores
+      float *dr5 = col + D_R5 * stride;
+      dr5[0] = dx0;
+      dr5[stride] = dx1;
+      dr5[2 * stride] = dx2;
+      dr5[3 * stride] = 0.f;
+      __syncwarp();
+      warp_back<4, kWidth>(sW + PL.r5, 4, wcol, stride, D_R5, R_RH + 3 * kWidth, D_R + 3 * kWidth, false);
+      warp_back<kWidth, kWidth>(sW + PL.r4, kPadRow, wcol, stride, D_R + 3 * kWidth, R_RH + 2 * kWidth,
+                                D_R + 2 * kWidth, false);
+      warp_back<kWidth, kResGammaPad>(sW + PL.r4 + kWidth * kPadRow, kPadRow, wcol, stride, D_R + 3 * kWidth, -1,
+                                      R_DGAM, false);
+      warp_back<kWidth, kWidth>(sW + PL.r3, kPadRow, wcol, stride, D_R + 2 * kWidth, R_RH + 1 * kWidth,
+                                D_R + 1 * kWidth, false);
+      warp_back<kWidth, kWidth>(sW + PL.r2, kPadRow, wcol, stride, D_R + 1 * kWidth, R_RH + 0 * kWidth,
+                                D_R + 0 * kWidth, false);
+      // dL/dgamma += W1_gamma^T delta1 (the pose columns of W1 are reduced per frame below)
+      warp_back<kWidth, kResGammaPad>(sW + PL.r1, kPadRow, wcol, stride, D_R, -1, R_DGAM, true);
+      __syncwarp();
+      if (active) {
           // through gamma: d gamma / d x_skel
           const float *dg = col + R_DGAM * stride;
           const float xh[3] = {(xs0 - P.box_c[0]) * P.box_ih[0], (xs1 - P.box_c[1]) * P.box_ih[1],
@@ -545,7 +690,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           ds0 += dh[0] * P.box_ih[0];
           ds1 += dh[1] * P.box_ih[1];
           ds2 += dh[2] * P.box_ih[2];
-        }
+      }
+    }
+    if (active) {
         // ---------------- inverse-LBS backward: scatter into the weight volume
         // and, for the pose refiner, dL/dp_i of each candidate p_i = G_i x:
         //   x_skel = sum_i w_i p_i / D,  w_i = W_i(p_i)
@@ -592,7 +739,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
             }
           }
         }
-      }
     }
     if (!active) {  // contributes nothing: zero every row the warp reduction reads
       for (int q = 0; q < kRows; ++q) col[q * stride] = 0.f;
@@ -887,6 +1033,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.rw = rows;
   T.dG = refine ? s->f_dG : nullptr;
   T.dG_smem = dG_smem ? 1 : 0;
+  T.pl = pad_layout(s->lay, (int)s->hidden);
   T.pred = b->pred_rgb;
   T.grad_rgb = fwd_only ? nullptr : b->grad_rgb;
   T.forward_only = fwd_only ? 1 : 0;
@@ -908,7 +1055,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
     }
     return NR_OK;
   }
-  const size_t smem_b = sizeof(float) * (s->lay.total + (dG_smem ? n_dG : 0));
+  const size_t smem_b = sizeof(float) * (T.pl.total + (dG_smem ? n_dG : 0));
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);
   NR_CHECK_CUDA(cudaGetLastError());
