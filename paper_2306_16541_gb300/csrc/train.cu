@@ -413,30 +413,6 @@ __device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, 
   }
 }
 
-// y = W x + b over the padded copy (row k of W^T at Wt + k * rs), x in the thread's column.
-template <int OUT>
-__device__ __forceinline__ void dense_rs(const float *__restrict__ Wt, int rs, const float *__restrict__ b,
-                                         const float *__restrict__ col, int in, int stride, float (&y)[OUT],
-                                         bool init = true) {
-  if (init) {
-#pragma unroll
-    for (int j = 0; j < OUT; ++j) y[j] = b[j];
-  }
-#pragma unroll 2
-  for (int k = 0; k < in; ++k) {
-    const float xk = col[k * stride];
-    const float4 *row = reinterpret_cast<const float4 *>(Wt + k * rs);
-#pragma unroll
-    for (int j = 0; j < OUT / 4; ++j) {
-      const float4 w = row[j];
-      y[4 * j + 0] = fmaf(xk, w.x, y[4 * j + 0]);
-      y[4 * j + 1] = fmaf(xk, w.y, y[4 * j + 1]);
-      y[4 * j + 2] = fmaf(xk, w.z, y[4 * j + 2]);
-      y[4 * j + 3] = fmaf(xk, w.w, y[4 * j + 3]);
-    }
-  }
-}
-
 // The backward of one layer for the warp's 32 samples on the tensor cores:
 //   out[s][i] = (sum_o W^T[i][o] delta[s][o]) * (h[s][i] > 0)     (no mask when r_h < 0)
 // as C = W^T D^T with M = IN (16-row tiles of inputs), N = the 32 samples (4 tiles of 8),
@@ -499,6 +475,72 @@ __device__ __forceinline__ void warp_back(const float *__restrict__ Wt, int rs, 
   __syncwarp();   // the next layer reads these rows through other lanes
 }
 
+// The forward of one layer for the warp's 32 samples on the tensor cores:
+//   out[s][o] = act(sum_i W[o][i] x[s][i] + bias)
+// as C = W X^T with M = OUT (16-row tiles of outputs; rows past OUT are zero), N = the 32
+// samples, K = IN + IN2 inputs (x rows r_in.. then r_in2.. for a second input segment, i.e.
+// rows IN.. of W^T); m16n8k8 TF32 MMAs, three per step.  bias is b[o], or fb[frame][o] with
+// each sample's frame taken from the lane that owns the sample (fr).  Outputs past OUT are not
+// written.  Every lane of the warp must take part.
+template <int OUT, int IN, int IN2>
+__device__ __forceinline__ void warp_fwd(const float *__restrict__ Wt, int rs, float *wcol, int stride, int r_in,
+                                         int r_in2, const float *__restrict__ b, const float *__restrict__ fb, int fr,
+                                         bool relu, int r_out) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  constexpr int MT = (OUT + 15) / 16, KS = (IN + IN2) / 8;
+  float acc[MT][4][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+#pragma unroll 1
+  for (int ks = 0; ks < KS; ++ks) {
+    const int i0 = 8 * ks + t, i1 = i0 + 4;
+    const int x0 = i0 < IN ? r_in + i0 : r_in2 + (i0 - IN), x1 = i1 < IN ? r_in + i1 : r_in2 + (i1 - IN);
+    uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      tf32_split(wcol[x0 * stride + 8 * n + g], bh[n][0], bl[n][0]);
+      tf32_split(wcol[x1 * stride + 8 * n + g], bh[n][1], bl[n][1]);
+    }
+    const float *w0 = Wt + i0 * rs, *w1 = Wt + i1 * rs;
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int o0 = 16 * m + g, o8 = o0 + 8;
+      uint32_t ah[4], al[4];
+      tf32_split(o0 < OUT ? w0[o0] : 0.f, ah[0], al[0]);
+      tf32_split(o8 < OUT ? w0[o8] : 0.f, ah[1], al[1]);
+      tf32_split(o0 < OUT ? w1[o0] : 0.f, ah[2], al[2]);
+      tf32_split(o8 < OUT ? w1[o8] : 0.f, ah[3], al[3]);
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        mma_tf32(acc[m][n], al, bh[n]);
+        mma_tf32(acc[m][n], ah, bl[n]);
+        mma_tf32(acc[m][n], ah, bh[n]);
+      }
+    }
+  }
+  // acc[m][n] = C[16m + g][8n + 2t], C[16m + g][8n + 2t + 1], C[16m + g + 8][8n + 2t], C[16m + g + 8][8n + 2t + 1]
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int s0 = 8 * n + 2 * t;
+    const int f0 = __shfl_sync(0xffffffffu, fr, s0), f1 = __shfl_sync(0xffffffffu, fr, s0 + 1);
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = 16 * m + g + (q >= 2 ? 8 : 0), smp = s0 + (q & 1);
+        if (o >= OUT) continue;
+        float v = acc[m][n][q] + (fb ? fb[(size_t)((q & 1) ? f1 : f0) * kWidth + o] : b[o]);
+        if (relu) v = fmaxf(v, 0.f);
+        wcol[(r_out + o) * stride + smp] = v;
+      }
+  }
+  __syncwarp();   // the next step reads these rows through other lanes
+}
+
 // One thread per sample: forward recompute (activations into the thread's scratch
 // column), backward, scatter-adds, then the warp's weight-gradient reduction.
 __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P, TrainDev T) {
@@ -542,62 +584,68 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     const float *G = T.fG + (size_t)f * kBones * 12;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     float xs0 = 0.f, xs1 = 0.f, xs2 = 0.f, S = 0.f, xf0 = 0.f, xf1 = 0.f, xf2 = 0.f, dS_alpha = 0.f;
+    // ---------------- forward recompute: per-sample gathers, warp-level MLP layers
     if (active) {
-      // ---------------- forward recompute (CUDA cores, one sample per thread)
       s = __ldcs(T.samp + j);
       lbs_warp(P, G, s.x, s.y, s.z, xs0, xs1, xs2, S);
       xf0 = xs0;
       xf1 = xs1;
       xf2 = xs2;
-      float y[kWidth];
-      const float *bias1 = T.fbias1 + (size_t)f * kWidth;
       pos_enc(P, xs0, xs1, xs2, col + R_GAM * stride, stride);
+    } else {
+      for (int q = 0; q < kResGammaPad; ++q) col[(R_GAM + q) * stride] = 0.f;
+    }
+    __syncwarp();
+    if (P.res_enabled) {
+      warp_fwd<kWidth, kResGammaPad, 0>(sW + PL.r1, kPadRow, wcol, stride, R_GAM, 0, nullptr, T.fbias1, (int)f,
+                                        true, R_RH + 0 * kWidth);
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.r2, kPadRow, wcol, stride, R_RH + 0 * kWidth, 0, sW + PL.r2b, nullptr, 0,
+                                  true, R_RH + 1 * kWidth);
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.r3, kPadRow, wcol, stride, R_RH + 1 * kWidth, 0, sW + PL.r3b, nullptr, 0,
+                                  true, R_RH + 2 * kWidth);
+      warp_fwd<kWidth, kWidth, kResGammaPad>(sW + PL.r4, kPadRow, wcol, stride, R_RH + 2 * kWidth, R_GAM, sW + PL.r4b,
+                                             nullptr, 0, true, R_RH + 3 * kWidth);
+      // x_res into the (not yet used) rows of the residual output's delta
+      warp_fwd<4, kWidth, 0>(sW + PL.r5, 4, wcol, stride, R_RH + 3 * kWidth, 0, sW + PL.r5b, nullptr, 0, false, D_R5);
+    }
+    bool inside = false;
+    if (active) {
       if (P.res_enabled) {
-        dense_rs<kWidth>(sW + PL.r1, kPadRow, bias1, col + R_GAM * stride, kResGammaPad, stride, y);
-        store_relu(y, col + (R_RH + 0 * kWidth) * stride, stride);
-        dense_rs<kWidth>(sW + PL.r2, kPadRow, sW + PL.r2b, col + (R_RH + 0 * kWidth) * stride, kWidth, stride, y);
-        store_relu(y, col + (R_RH + 1 * kWidth) * stride, stride);
-        dense_rs<kWidth>(sW + PL.r3, kPadRow, sW + PL.r3b, col + (R_RH + 1 * kWidth) * stride, kWidth, stride, y);
-        store_relu(y, col + (R_RH + 2 * kWidth) * stride, stride);
-        dense_rs<kWidth>(sW + PL.r4, kPadRow, sW + PL.r4b, col + (R_RH + 2 * kWidth) * stride, kWidth, stride, y);
-        dense_rs<kWidth>(sW + PL.r4 + kWidth * kPadRow, kPadRow, nullptr, col + R_GAM * stride, kResGammaPad, stride,
-                         y, false);
-        store_relu(y, col + (R_RH + 3 * kWidth) * stride, stride);
-        float o3[4];
-        dense_rs<4>(sW + PL.r5, 4, sW + PL.r5b, col + (R_RH + 3 * kWidth) * stride, kWidth, stride, o3);
-        xf0 += o3[0];
-        xf1 += o3[1];
-        xf2 += o3[2];
+        xf0 += col[(D_R5 + 0) * stride];
+        xf1 += col[(D_R5 + 1) * stride];
+        xf2 += col[(D_R5 + 2) * stride];
       } else {
         for (int q = 0; q < 4 * kWidth; ++q) col[(R_RH + q) * stride] = 0.f;
       }
-      const bool inside = hash_encode(P, xf0, xf1, xf2, col + R_ENC * stride, stride);
-      dense_rs<kWidth>(sW + PL.c0, kPadRow, sW + PL.c0b, col + R_ENC * stride, kMlpIn, stride, y);
-      store_relu(y, col + R_CH * stride, stride);
-      for (int l = 1; l < H; ++l) {
-        dense_rs<kWidth>(sW + PL.ch[l - 1], kPadRow, sW + PL.chb[l - 1], col + (R_CH + (l - 1) * kWidth) * stride,
-                         kWidth, stride, y);
-        store_relu(y, col + (R_CH + l * kWidth) * stride, stride);
-      }
-      float o[4];
-      dense_rs<4>(sW + PL.cl, 4, sW + PL.clb, col + (R_CH + (H - 1) * kWidth) * stride, kWidth, stride, o);
-      active = inside;
-      if (active) {
-        // ---------------- alpha, rgb, sigma
-        const float sig = softplusf_(o[3]);
-        const float e = expf(-sig * s.w);
-        const float lk = fminf(S, 1.f);
-        const float dsig = g4.w * s.w * e * lk;
-        dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
-        const float gc[3] = {g4.x, g4.y, g4.z};
-        float *dcl = col + (D_C + H * kWidth) * stride;
+      inside = hash_encode(P, xf0, xf1, xf2, col + R_ENC * stride, stride);
+    } else {
+      for (int q = 0; q < kMlpIn; ++q) col[(R_ENC + q) * stride] = 0.f;
+    }
+    __syncwarp();
+    warp_fwd<kWidth, kMlpIn, 0>(sW + PL.c0, kPadRow, wcol, stride, R_ENC, 0, sW + PL.c0b, nullptr, 0, true, R_CH);
+    for (int l = 1; l < H; ++l)
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.ch[l - 1], kPadRow, wcol, stride, R_CH + (l - 1) * kWidth, 0,
+                                  sW + PL.chb[l - 1], nullptr, 0, true, R_CH + l * kWidth);
+    // the canonical output o into the rows of its delta, read back by each sample's thread
+    warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
+                           D_C + H * kWidth);
+    active = active && inside;
+    if (active) {
+      // ---------------- alpha, rgb, sigma
+      float *dcl = col + (D_C + H * kWidth) * stride;
+      const float o[4] = {dcl[0], dcl[stride], dcl[2 * stride], dcl[3 * stride]};
+      const float sig = softplusf_(o[3]);
+      const float e = expf(-sig * s.w);
+      const float lk = fminf(S, 1.f);
+      const float dsig = g4.w * s.w * e * lk;
+      dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
+      const float gc[3] = {g4.x, g4.y, g4.z};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float c = sigmoidf_(o[k]);
-          dcl[k * stride] = gc[k] * c * (1.f - c);
-        }
-        dcl[3 * stride] = dsig * sigmoidf_(o[3]);
+      for (int k = 0; k < 3; ++k) {
+        const float c = sigmoidf_(o[k]);
+        dcl[k * stride] = gc[k] * c * (1.f - c);
       }
+      dcl[3 * stride] = dsig * sigmoidf_(o[3]);
     }
     if (!active)
       for (int k = 0; k < 4; ++k) col[(D_C + H * kWidth + k) * stride] = 0.f;
