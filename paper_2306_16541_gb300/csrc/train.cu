@@ -31,8 +31,8 @@ struct Rows {
   int rh;      // residual h1..h4          4 x 64
   int enc;     // hash encoding            32
   int ch;      // canonical h1..hH         H x 64
-  int dc;      // canonical deltas h1..hH  H x 64, then the output's 4
-  int dr;      // residual deltas h1..h4   4 x 64
+  int db;      // two 64-row delta buffers, used in turn by both MLPs' backward
+  int dcl;     // canonical output delta   4
   int dr5;     // residual output delta    4
   int denc;    // dL/d encoding            32
   int dgam;    // dL/d gamma               48
@@ -48,8 +48,8 @@ static Rows make_rows(int H) {
   r.rh = o; o += 4 * kWidth;
   r.enc = o; o += kMlpIn;
   r.ch = o; o += H * kWidth;
-  r.dc = o; o += H * kWidth + 4;
-  r.dr = o; o += 4 * kWidth;
+  r.db = o; o += 2 * kWidth;
+  r.dcl = o; o += 4;
   r.dr5 = o; o += 4;
   r.denc = o; o += kMlpIn;
   r.dgam = o; o += kResGammaPad;
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
   const int stride = blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Rows &RW = T.rw;
-  const int R_GAM = RW.gam, R_RH = RW.rh, R_ENC = RW.enc, R_CH = RW.ch, D_C = RW.dc, D_R = RW.dr, D_R5 = RW.dr5,
+  const int R_GAM = RW.gam, R_RH = RW.rh, R_ENC = RW.enc, R_CH = RW.ch, D_B = RW.db, D_CL = RW.dcl, D_R5 = RW.dr5,
             R_DENC = RW.denc, R_DGAM = RW.dgam, R_DP = RW.dp, R_XS = RW.xs, kRows = RW.total;
   float *colbase = T.scratch + (size_t)blockIdx.x * kRows * stride;
   float *col = colbase + threadIdx.x;                  // this thread's column
@@ -628,11 +628,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
                                   sW + PL.chb[l - 1], nullptr, 0, true, R_CH + l * kWidth);
     // the canonical output o into the rows of its delta, read back by each sample's thread
     warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
-                           D_C + H * kWidth);
+                           D_CL);
     active = active && inside;
     if (active) {
       // ---------------- alpha, rgb, sigma
-      float *dcl = col + (D_C + H * kWidth) * stride;
+      float *dcl = col + (D_CL) * stride;
       const float o[4] = {dcl[0], dcl[stride], dcl[2 * stride], dcl[3 * stride]};
       const float sig = softplusf_(o[3]);
       const float e = expf(-sig * s.w);
@@ -648,15 +648,24 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       dcl[3 * stride] = dsig * sigmoidf_(o[3]);
     }
     if (!active)
-      for (int k = 0; k < 4; ++k) col[(D_C + H * kWidth + k) * stride] = 0.f;
+      for (int k = 0; k < 4; ++k) col[(D_CL + k) * stride] = 0.f;
     __syncwarp();
-    // ---------------- canonical MLP backward: the warp's 32 samples on the tensor cores
-    warp_back<4, kWidth>(sW + PL.cl, 4, wcol, stride, D_C + H * kWidth, R_CH + (H - 1) * kWidth,
-                         D_C + (H - 1) * kWidth, false);
-    for (int l = H - 1; l >= 1; --l)
-      warp_back<kWidth, kWidth>(sW + PL.ch[l - 1], kPadRow, wcol, stride, D_C + l * kWidth, R_CH + (l - 1) * kWidth,
-                                D_C + (l - 1) * kWidth, false);
-    warp_back<kWidth, kMlpIn>(sW + PL.c0, kPadRow, wcol, stride, D_C, -1, R_DENC, false);
+    // ---------------- canonical MLP backward: the warp's 32 samples on the tensor cores, each
+    // layer's weight gradient summed as soon as its delta exists (two delta buffers in turn)
+    {
+      int cur = D_B, nxt = D_B + kWidth;
+      warp_back<4, kWidth>(sW + PL.cl, 4, wcol, stride, D_CL, R_CH + (H - 1) * kWidth, cur, false);
+      wgrad4(wcol, stride, R_CH + (H - 1) * kWidth, D_CL, 4, acc, Ly.cl, Ly.clb);
+      for (int l = H - 1; l >= 1; --l) {
+        warp_back<kWidth, kWidth>(sW + PL.ch[l - 1], kPadRow, wcol, stride, cur, R_CH + (l - 1) * kWidth, nxt, false);
+        wgrad64(wcol, stride, R_CH + (l - 1) * kWidth, kWidth, cur, acc, Ly.ch[l - 1], Ly.chb[l - 1], true);
+        const int tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+      warp_back<kWidth, kMlpIn>(sW + PL.c0, kPadRow, wcol, stride, cur, -1, R_DENC, false);
+      wgrad64(wcol, stride, R_ENC, kMlpIn, cur, acc, Ly.c0, Ly.c0b, true);
+    }
     __syncwarp();
     float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
     if (active) {
@@ -707,17 +716,45 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       dr5[2 * stride] = dx2;
       dr5[3 * stride] = 0.f;
       __syncwarp();
-      warp_back<4, kWidth>(sW + PL.r5, 4, wcol, stride, D_R5, R_RH + 3 * kWidth, D_R + 3 * kWidth, false);
-      warp_back<kWidth, kWidth>(sW + PL.r4, kPadRow, wcol, stride, D_R + 3 * kWidth, R_RH + 2 * kWidth,
-                                D_R + 2 * kWidth, false);
-      warp_back<kWidth, kResGammaPad>(sW + PL.r4 + kWidth * kPadRow, kPadRow, wcol, stride, D_R + 3 * kWidth, -1,
-                                      R_DGAM, false);
-      warp_back<kWidth, kWidth>(sW + PL.r3, kPadRow, wcol, stride, D_R + 2 * kWidth, R_RH + 1 * kWidth,
-                                D_R + 1 * kWidth, false);
-      warp_back<kWidth, kWidth>(sW + PL.r2, kPadRow, wcol, stride, D_R + 1 * kWidth, R_RH + 0 * kWidth,
-                                D_R + 0 * kWidth, false);
+      const int b0 = D_B, b1 = D_B + kWidth;   // delta4 -> b0, delta3 -> b1, delta2 -> b0, delta1 -> b1
+      warp_back<4, kWidth>(sW + PL.r5, 4, wcol, stride, D_R5, R_RH + 3 * kWidth, b0, false);
+      wgrad4(wcol, stride, R_RH + 3 * kWidth, D_R5, 3, acc, Ly.r5, Ly.r5b);
+      warp_back<kWidth, kWidth>(sW + PL.r4, kPadRow, wcol, stride, b0, R_RH + 2 * kWidth, b1, false);
+      warp_back<kWidth, kResGammaPad>(sW + PL.r4 + kWidth * kPadRow, kPadRow, wcol, stride, b0, -1, R_DGAM, false);
+      wgrad64(wcol, stride, R_RH + 2 * kWidth, kWidth, b0, acc, Ly.r4, Ly.r4b, true);
+      wgrad64(wcol, stride, R_GAM, kResGammaPad, b0, acc, Ly.r4 + kWidth * kWidth, 0, false);
+      warp_back<kWidth, kWidth>(sW + PL.r3, kPadRow, wcol, stride, b1, R_RH + 1 * kWidth, b0, false);
+      wgrad64(wcol, stride, R_RH + 1 * kWidth, kWidth, b1, acc, Ly.r3, Ly.r3b, true);
+      warp_back<kWidth, kWidth>(sW + PL.r2, kPadRow, wcol, stride, b0, R_RH + 0 * kWidth, b1, false);
+      wgrad64(wcol, stride, R_RH + 0 * kWidth, kWidth, b0, acc, Ly.r2, Ly.r2b, true);
       // dL/dgamma += W1_gamma^T delta1 (the pose columns of W1 are reduced per frame below)
-      warp_back<kWidth, kResGammaPad>(sW + PL.r1, kPadRow, wcol, stride, D_R, -1, R_DGAM, true);
+      warp_back<kWidth, kResGammaPad>(sW + PL.r1, kPadRow, wcol, stride, b1, -1, R_DGAM, true);
+      wgrad64(wcol, stride, R_GAM, kResGammaPad, b1, acc, Ly.r1, Ly.r1b, true);
+      {  // per-frame sums of delta1 (for W_Omega): lane owns rows lane, lane + 32
+        const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
+        const float *d0 = wcol + (b1 + lane) * stride, *d1 = wcol + (b1 + lane + 32) * stride;
+        int cur = -1;
+        float s0 = 0.f, s1 = 0.f;
+        for (int sI = 0; sI < 32; ++sI) {
+          const uint32_t jj = j0 + sI;
+          if (jj >= n) break;
+          const int fr = (int)T.frame_id[jj / T.S];
+          if (fr != cur) {
+            if (cur >= 0) {
+              atomicAdd(accF + cur * kWidth + lane, s0);
+              atomicAdd(accF + cur * kWidth + lane + 32, s1);
+            }
+            cur = fr;
+            s0 = s1 = 0.f;
+          }
+          s0 += d0[sI];
+          s1 += d1[sI];
+        }
+        if (cur >= 0) {
+          atomicAdd(accF + cur * kWidth + lane, s0);
+          atomicAdd(accF + cur * kWidth + lane + 32, s1);
+        }
+      }
       __syncwarp();
       if (active) {
           // through gamma: d gamma / d x_skel
@@ -788,49 +825,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           }
         }
     }
-    if (!active) {  // contributes nothing: zero every row the warp reduction reads
-      for (int q = 0; q < kRows; ++q) col[q * stride] = 0.f;
-    } else if (!P.res_enabled) {
-      for (int q = D_R; q < D_R5 + 4; ++q) col[q * stride] = 0.f;
-    }
+    if (T.dG && !active)   // the refiner's reduction reads these rows of every lane
+      for (int q = 0; q < 3 * kBones + 3; ++q) col[(R_DP + q) * stride] = 0.f;
     __syncwarp();
-    // ---------------- warp-level weight gradients (private accumulator)
-    wgrad64(wcol, stride, R_ENC, kMlpIn, D_C, acc, Ly.c0, Ly.c0b, true);
-    for (int l = 1; l < H; ++l)
-      wgrad64(wcol, stride, R_CH + (l - 1) * kWidth, kWidth, D_C + l * kWidth, acc, Ly.ch[l - 1], Ly.chb[l - 1], true);
-    wgrad4(wcol, stride, R_CH + (H - 1) * kWidth, D_C + H * kWidth, 4, acc, Ly.cl, Ly.clb);
-    if (P.res_enabled) {
-      wgrad64(wcol, stride, R_GAM, kResGammaPad, D_R, acc, Ly.r1, Ly.r1b, true);
-      wgrad64(wcol, stride, R_RH + 0 * kWidth, kWidth, D_R + 1 * kWidth, acc, Ly.r2, Ly.r2b, true);
-      wgrad64(wcol, stride, R_RH + 1 * kWidth, kWidth, D_R + 2 * kWidth, acc, Ly.r3, Ly.r3b, true);
-      wgrad64(wcol, stride, R_RH + 2 * kWidth, kWidth, D_R + 3 * kWidth, acc, Ly.r4, Ly.r4b, true);
-      wgrad64(wcol, stride, R_GAM, kResGammaPad, D_R + 3 * kWidth, acc, Ly.r4 + kWidth * kWidth, 0, false);
-      wgrad4(wcol, stride, R_RH + 3 * kWidth, D_R5, 3, acc, Ly.r5, Ly.r5b);
-      // per-frame sums of delta1 (for W_Omega): lane owns rows lane, lane + 32
-      const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
-      const float *d0 = wcol + (D_R + lane) * stride, *d1 = wcol + (D_R + lane + 32) * stride;
-      int cur = -1;
-      float s0 = 0.f, s1 = 0.f;
-      for (int sI = 0; sI < 32; ++sI) {
-        const uint32_t jj = j0 + sI;
-        if (jj >= n) break;
-        const int fr = (int)T.frame_id[jj / T.S];
-        if (fr != cur) {
-          if (cur >= 0) {
-            atomicAdd(accF + cur * kWidth + lane, s0);
-            atomicAdd(accF + cur * kWidth + lane + 32, s1);
-          }
-          cur = fr;
-          s0 = s1 = 0.f;
-        }
-        s0 += d0[sI];
-        s1 += d1[sI];
-      }
-      if (cur >= 0) {
-        atomicAdd(accF + cur * kWidth + lane, s0);
-        atomicAdd(accF + cur * kWidth + lane + 32, s1);
-      }
-    }
     if (T.dG) {
       // dL/dG_i of each frame: dR_i += dp_i x^T, dt_i += dp_i over the warp's 32 samples;
       // lane owns 9 of the 24 x 12 entries and sums them per run of equal frames
