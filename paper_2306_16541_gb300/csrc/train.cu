@@ -177,47 +177,6 @@ __global__ void __launch_bounds__(256) train_samples_kernel(TrainDev T, float bx
   T.samp[q] = make_float4(o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2], tn - t);
 }
 
-// ------------------------------------------------------------ forward field
-// The float32 field of render.cu, with the pose of each sample's frame.
-__global__ void __launch_bounds__(192, 1) train_fwd_kernel(FieldParams P, TrainDev T) {
-  extern __shared__ float4 smem4[];
-  float *sW = reinterpret_cast<float *>(smem4);
-  float *sCol = sW + P.lay.total;
-  for (int i = threadIdx.x; i < P.lay.total / 4; i += blockDim.x)
-    reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(P.blob) + i);
-  __syncthreads();
-  const int stride = blockDim.x;
-  float *hcol = sCol + threadIdx.x;
-  float *gcol = hcol + kWidth * stride;
-  const uint32_t n = T.n_rays * T.S;
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t r = j / T.S;
-    if (!T.raycnt[r]) {
-      T.out[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    const uint32_t f = T.frame_id[r];
-    const float *G = T.fG + (size_t)f * kBones * 12;
-    const float4 s = T.samp[j];
-    float s0, s1, s2, S;
-    lbs_warp(P, G, s.x, s.y, s.z, s0, s1, s2, S);
-    float f0 = s0, f1 = s1, f2 = s2;
-    if (P.res_enabled) {
-      pos_enc(P, s0, s1, s2, gcol, stride);
-      float r0, r1, r2;
-      residual_f32(P, sW, T.fbias1 + (size_t)f * kWidth, gcol, hcol, stride, r0, r1, r2);
-      f0 += r0;
-      f1 += r1;
-      f2 += r2;
-    }
-    const bool inside = hash_encode(P, f0, f1, f2, hcol, stride);
-    float o[4];
-    canonical_f32(P, sW, hcol, stride, o);
-    const float a = inside ? (1.f - expf(-softplusf_(o[3]) * s.w)) * fminf(S, 1.f) : 0.f;
-    T.out[j] = make_float4(sigmoidf_(o[0]), sigmoidf_(o[1]), sigmoidf_(o[2]), a);
-  }
-}
-
 // ------------------------------------------------- compositing and its adjoint
 // Per ray: C = sum_i T_i alpha_i c_i + T_S bg, T_{i+1} = T_i (1 - alpha_i) (Eq. 3),
 // loss term sum_k (C_k - C_gt,k)^2 / (3 N), g = dL/dC.  The reverse scan keeps
@@ -539,6 +498,95 @@ __device__ __forceinline__ void warp_fwd(const float *__restrict__ Wt, int rs, f
       }
   }
   __syncwarp();   // the next step reads these rows through other lanes
+}
+
+// ------------------------------------------------------------ forward field
+// The float32 field with the pose of each sample's frame, laid out like the backward
+// kernel: per-sample gathers (LBS warp, PE, hash encoding) one sample per thread, both MLPs
+// as warp-level tensor-core layers over the samples' scratch columns (float32 accuracy).
+// Writes (r, g, b, alpha) per sample slot (zero for a ray that misses the box).
+__global__ void __launch_bounds__(kBwdThreads, 1) train_fwd_kernel(FieldParams P, TrainDev T) {
+  extern __shared__ float4 smem4[];
+  float *sW = reinterpret_cast<float *>(smem4);        // the weights in the padded layout T.pl
+  for (int q = 0; q < T.pl.n_seg; ++q) {
+    const PadSeg &sg = T.pl.seg[q];
+    for (int i = threadIdx.x; i < sg.rows * sg.cols; i += blockDim.x) {
+      const int rr = i / sg.cols, cc = i - rr * sg.cols;
+      sW[sg.dst + rr * sg.dstride + cc] = __ldg(P.blob + sg.src + i);
+    }
+  }
+  __syncthreads();
+  const PadLay &PL = T.pl;
+  const int stride = blockDim.x;
+  const int warp = threadIdx.x >> 5;
+  const Rows &RW = T.rw;
+  const int R_GAM = RW.gam, R_RH = RW.rh, R_ENC = RW.enc, R_CH = RW.ch, D_CL = RW.dcl, D_R5 = RW.dr5;
+  float *colbase = T.scratch + (size_t)blockIdx.x * RW.total * stride;
+  float *col = colbase + threadIdx.x;
+  float *wcol = colbase + warp * 32;
+  const int H = P.hidden;
+  const uint32_t n = T.n_rays * T.S;
+  const uint32_t step = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (n + step - 1) / step;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t j = it * step + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t r = j < n ? j / T.S : 0;
+    const bool active = j < n && T.raycnt[r] != 0;
+    const uint32_t f = active ? T.frame_id[r] : 0;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float S = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    if (active) {
+      s = T.samp[j];
+      float s0, s1, s2;
+      lbs_warp(P, T.fG + (size_t)f * kBones * 12, s.x, s.y, s.z, s0, s1, s2, S);
+      f0 = s0;
+      f1 = s1;
+      f2 = s2;
+      pos_enc(P, s0, s1, s2, col + R_GAM * stride, stride);
+    } else {
+      for (int q = 0; q < kResGammaPad; ++q) col[(R_GAM + q) * stride] = 0.f;
+    }
+    __syncwarp();
+    if (P.res_enabled) {
+      warp_fwd<kWidth, kResGammaPad, 0>(sW + PL.r1, kPadRow, wcol, stride, R_GAM, 0, nullptr, T.fbias1, (int)f,
+                                        true, R_RH + 0 * kWidth);
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.r2, kPadRow, wcol, stride, R_RH + 0 * kWidth, 0, sW + PL.r2b, nullptr, 0,
+                                  true, R_RH + 1 * kWidth);
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.r3, kPadRow, wcol, stride, R_RH + 1 * kWidth, 0, sW + PL.r3b, nullptr, 0,
+                                  true, R_RH + 2 * kWidth);
+      warp_fwd<kWidth, kWidth, kResGammaPad>(sW + PL.r4, kPadRow, wcol, stride, R_RH + 2 * kWidth, R_GAM, sW + PL.r4b,
+                                             nullptr, 0, true, R_RH + 3 * kWidth);
+      warp_fwd<4, kWidth, 0>(sW + PL.r5, 4, wcol, stride, R_RH + 3 * kWidth, 0, sW + PL.r5b, nullptr, 0, false, D_R5);
+    }
+    bool inside = false;
+    if (active) {
+      if (P.res_enabled) {
+        f0 += col[(D_R5 + 0) * stride];
+        f1 += col[(D_R5 + 1) * stride];
+        f2 += col[(D_R5 + 2) * stride];
+      }
+      inside = hash_encode(P, f0, f1, f2, col + R_ENC * stride, stride);
+    } else {
+      for (int q = 0; q < kMlpIn; ++q) col[(R_ENC + q) * stride] = 0.f;
+    }
+    __syncwarp();
+    warp_fwd<kWidth, kMlpIn, 0>(sW + PL.c0, kPadRow, wcol, stride, R_ENC, 0, sW + PL.c0b, nullptr, 0, true, R_CH);
+    for (int l = 1; l < H; ++l)
+      warp_fwd<kWidth, kWidth, 0>(sW + PL.ch[l - 1], kPadRow, wcol, stride, R_CH + (l - 1) * kWidth, 0,
+                                  sW + PL.chb[l - 1], nullptr, 0, true, R_CH + l * kWidth);
+    warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
+                           D_CL);
+    if (j < n) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) {
+        const float o0 = col[D_CL * stride], o1 = col[(D_CL + 1) * stride], o2 = col[(D_CL + 2) * stride],
+                    o3 = col[(D_CL + 3) * stride];
+        const float a = inside ? (1.f - expf(-softplusf_(o3) * s.w)) * fminf(S, 1.f) : 0.f;
+        v = make_float4(sigmoidf_(o0), sigmoidf_(o1), sigmoidf_(o2), a);
+      }
+      T.out[j] = v;
+    }
+  }
 }
 
 // One thread per sample: forward recompute (activations into the thread's scratch
@@ -1086,9 +1134,9 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   train_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
                                                                      s->bmax[1], s->bmax[2]);
   NR_CHECK_CUDA(cudaGetLastError());
-  const size_t smem_f = sizeof(float) * (s->lay.total + (size_t)(kWidth + kResGammaPad) * 192);
+  const size_t smem_f = sizeof(float) * T.pl.total;
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
-  train_fwd_kernel<<<blocks, 192, smem_f, st>>>(P, T);
+  train_fwd_kernel<<<blocks, kBwdThreads, smem_f, st>>>(P, T);
   NR_CHECK_CUDA(cudaGetLastError());
   train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
   NR_CHECK_CUDA(cudaGetLastError());
