@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
     p.add_argument("--train-rays", type=int, default=1 << 18, help="rays per training batch")
+    p.add_argument("--train-full", action="store_true",
+                   help="with --train-only: train the pose refiner and CNN_skel as well (patch batches)")
     p.add_argument("--train-layout", choices=["uniform", "patch"], default="uniform",
                    help="uniform random pixels, or 6 patches of 20x20 per image with MSE weight 0.2")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
@@ -439,7 +441,9 @@ def run_ours(a):
     barrier(world)
     from paper_2306_16541_gb300 import nr
     if a.train_only:
-        print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays, layout=a.train_layout)}))
+        print(json.dumps({"train_step": train_bench(nr, local, a.train_steps, n=a.train_rays,
+                                                    layout="patch" if a.train_full else a.train_layout,
+                                                    full=a.train_full)}))
         return
     if a.sweep_only:
         print(json.dumps({"precision_sweep": sweep_bench(nr, local)}))

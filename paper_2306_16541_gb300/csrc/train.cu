@@ -881,6 +881,46 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       // lane owns 9 of the 24 x 12 entries and sums them per run of equal frames
       const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
       const int fl = j0 + lane < n ? (int)T.frame_id[(j0 + lane) / T.S] : -1;
+      const int f0 = __shfl_sync(0xffffffffu, fl, 0);
+      if (__all_sync(0xffffffffu, fl == f0) && f0 >= 0) {
+        // one frame in the warp: C[3i + r][c] = sum_s dp_i[s][r] (x_s, y_s, z_s, 1)[c] as one
+        // tensor-core product (M = 72 rows of dp in 16-row tiles, N = 4 columns padded to 8,
+        // K = the 32 samples; m16n8k8 TF32, three products per step)
+        const int g = lane >> 2, t = lane & 3;
+        float *dst = (T.dG_smem ? sdG : T.dG) + (size_t)f0 * kBones * 12;
+        uint32_t bh[4][2], bl[4][2];   // B[s][c] = (x, y, z, 1)[c] of sample s, zero for c >= 4
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const int s0 = 8 * ks + t;
+          const float v0 = g < 3 ? wcol[(R_XS + g) * stride + s0] : (g == 3 ? 1.f : 0.f);
+          const float v1 = g < 3 ? wcol[(R_XS + g) * stride + s0 + 4] : (g == 3 ? 1.f : 0.f);
+          tf32_split(v0, bh[ks][0], bl[ks][0]);
+          tf32_split(v1, bh[ks][1], bl[ks][1]);
+        }
+#pragma unroll 1
+        for (int mt = 0; mt < 5; ++mt) {
+          const int o0 = 16 * mt + g, o8 = o0 + 8;
+          float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const int s0 = 8 * ks + t;
+            uint32_t ah[4], al[4];
+            tf32_split(o0 < 3 * kBones ? wcol[(R_DP + o0) * stride + s0] : 0.f, ah[0], al[0]);
+            tf32_split(o8 < 3 * kBones ? wcol[(R_DP + o8) * stride + s0] : 0.f, ah[1], al[1]);
+            tf32_split(o0 < 3 * kBones ? wcol[(R_DP + o0) * stride + s0 + 4] : 0.f, ah[2], al[2]);
+            tf32_split(o8 < 3 * kBones ? wcol[(R_DP + o8) * stride + s0 + 4] : 0.f, ah[3], al[3]);
+            mma_tf32(c, al, bh[ks]);
+            mma_tf32(c, ah, bl[ks]);
+            mma_tf32(c, ah, bh[ks]);
+          }
+          // c = C[o0][2t], C[o0][2t + 1], C[o8][2t], C[o8][2t + 1]
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int o = q >= 2 ? o8 : o0, cc = 2 * t + (q & 1);
+            if (o < 3 * kBones && cc < 4 && c[q] != 0.f) atomicAdd(dst + (o / 3) * 12 + (o % 3) * 4 + cc, c[q]);
+          }
+        }
+      } else {
       for (int o = lane; o < kBones * 12; o += 32) {
         const int i = o / 12, rr = (o % 12) >> 2, c = o & 3;
         const float *dpr = wcol + (R_DP + 3 * i + rr) * stride;
@@ -898,6 +938,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           v = fmaf(dpr[sI], c < 3 ? xr[sI] : 1.f, v);
         }
         if (cur >= 0 && v != 0.f) atomicAdd((T.dG_smem ? sdG : T.dG) + cur * kBones * 12 + o, v);
+      }
       }
     }
     __syncwarp();
