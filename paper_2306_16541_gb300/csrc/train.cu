@@ -1,20 +1,23 @@
 // train.cu -- one training step (Sec. 5.2): stratified samples of a batch of
 // pixel rays, the float32 field forward, compositing with the squared-error
-// loss, the hand-written backward (compositing adjoint, canonical MLP, hash
-// scatter-add, residual MLP through the positional encoding, inverse-LBS
-// scatter-add into the weight volume) and Adam.
+// loss (or a caller's dL/dC), the hand-written backward (compositing adjoint,
+// canonical MLP, hash scatter-add, residual MLP through the positional
+// encoding, inverse-LBS scatter-add into the weight volume, and the pose
+// refiner's dL/dG) and Adam.
 //
-// Gradient accumulation without contention:
+// Work split:
+//   * the gathers and their adjoints (LBS warp, PE, hash encoding) run one
+//     sample per thread; each thread keeps its sample's activations and deltas
+//     in its own column of a scratch buffer (rows x threads per block);
+//   * both MLPs run per warp of 32 samples on the tensor cores -- forward
+//     layers W X^T, layer backprop W^T D^T, weight gradients D^T H -- as
+//     m16n8k8 TF32 MMAs with three products per step (hi/lo splits) for
+//     float32 accuracy, over a bank-padded shared-memory copy of the weights;
+//   * weight gradients of a warp go into its block's private accumulator
+//     (fire-and-forget atomics shared by the block's warps); one kernel sums
+//     the block accumulators at the end;
 //   * hash-table and weight-volume gradients are scattered with float2 /
-//     float atomics straight into the gradient buffers;
-//   * MLP weight gradients dW = sum_s delta_s (x) h_s are reduced per warp:
-//     after a tile of 32 samples, every lane owns two output rows of a layer
-//     and sums the 32 samples' products for them, then adds the result into
-//     its block's private accumulator (fire-and-forget atomics shared by the
-//     block's 4 warps only); one kernel sums the block accumulators at the end.
-//   * each thread keeps its forward activations and backward deltas in its
-//     own column of an L2-resident scratch buffer, which the warp reads back
-//     in the reduction.
+//     float atomics straight into the gradient buffers.
 #include <math.h>
 #include <string.h>
 
@@ -235,27 +238,6 @@ __global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
 }
 
 // ---------------------------------------------------------------- backward
-// delta_prev[k] = (sum_j Wt[k][j] delta[j]) * (h_prev[k] > 0), Wt = W^T ([in][OUT]).
-template <int OUT>
-__device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const float *dcol, int in, const float *hcol,
-                                           float *outcol, int stride) {
-  float d[OUT];
-#pragma unroll
-  for (int j = 0; j < OUT; ++j) d[j] = dcol[j * stride];
-#pragma unroll 2
-  for (int k = 0; k < in; ++k) {
-    const float4 *row = reinterpret_cast<const float4 *>(Wt + k * OUT);
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < OUT / 4; ++j) {
-      const float4 w = row[j];
-      acc = fmaf(w.x, d[4 * j], fmaf(w.y, d[4 * j + 1], fmaf(w.z, d[4 * j + 2], fmaf(w.w, d[4 * j + 3], acc))));
-    }
-    if (hcol) acc = hcol[k * stride] > 0.f ? acc : 0.f;
-    outcol[k * stride] = acc;
-  }
-}
-
 // TF32 with an error term: x = hi + lo, both exactly representable in tf32; a product
 // x y = hi_x hi_y + hi_x lo_y + lo_x hi_y up to a term below float32's rounding, so three
 // tensor-core products keep float32 accuracy ("3xTF32").
