@@ -148,9 +148,36 @@ def cpu_baseline(cfg, poses, n_pixels, seed=0):
     t0 = time.perf_counter()
     OR.render_pixels(cfg["subject"], P, poses[0], cam, px, py, True)
     dt = time.perf_counter() - t0
-    return dict(value=n_pixels / dt, unit=UNIT, cores=torch.get_num_threads(), kind="oracle",
+    # the same oracle on one core, on a smaller sample of the same pixels
+    threads = torch.get_num_threads()
+    n1 = max(256, n_pixels // 16)
+    torch.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        OR.render_pixels(cfg["subject"], P, poses[0], cam, px[:n1], py[:n1], True)
+        dt1 = time.perf_counter() - t1
+    finally:
+        torch.set_num_threads(threads)
+    return dict(value=n_pixels / dt, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"{n_pixels} random pixels of one 512x512 frame (128 samples each, occupancy; "
-                       f"FP64 torch CPU, no early termination), {dt:.1f} s")
+                       f"FP64 torch CPU, no early termination), {dt:.1f} s",
+                one_core={"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                          "sample": f"the first {n1} of those pixels, {dt1:.1f} s"},
+                host=_host_cpu())
+
+
+def _host_cpu() -> str:
+    """The host's CPU model and logical core count (from /proc/cpuinfo or lscpu)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{model or 'unknown CPU'}, {os.cpu_count()} logical cores"
 
 
 def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform", full=False):
