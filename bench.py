@@ -244,7 +244,8 @@ def train_bench(nr, device, steps, warmup=2, n=1 << 18, layout="uniform", full=F
     extra = ", pose refiner 4x256 + CNN_skel 1024-512-256-128-64" if full else ""
     return {"workload": f"16 frames 512x512, {n} rays ({shape}) x 128 samples, fp32 forward+backward+Adam{extra}",
             "lr": "1e-2 (hash, canonical MLP), 1e-3 (weight volume, residual MLP)",
-            "ms": statistics.mean(ms), "ms_min": min(ms), "steps": steps, "warmup": warmup,
+            "ms": statistics.mean(ms), "ms_min": min(ms), "ms_steps": [round(v, 2) for v in ms],
+            "steps": steps, "warmup": warmup,
             "rays_per_s": n / (statistics.mean(ms) / 1000.0),
             "samples_per_s": n * 128 / (statistics.mean(ms) / 1000.0),
             "loss_first": losses[0], "loss_last": losses[-1]}

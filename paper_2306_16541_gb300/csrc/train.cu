@@ -17,7 +17,9 @@
 //     (fire-and-forget atomics shared by the block's warps); one kernel sums
 //     the block accumulators at the end;
 //   * hash-table and weight-volume gradients are scattered with float2 /
-//     float atomics straight into the gradient buffers.
+//     float atomics straight into the gradient buffers;
+//   * thread slots visit the batch's rays in a scattered order (ray_of), so
+//     that the rays in flight together do not come from one image patch.
 #include <math.h>
 #include <string.h>
 
@@ -26,7 +28,8 @@
 
 namespace nr {
 
-constexpr int kBwdThreads = 256;
+constexpr int kBwdThreads = 384;   // ~165 registers a thread (512 threads at 128 measured slower)
+constexpr int kFwdThreads = 512;   // the forward fits 128, so twice the warps hide its gathers
 
 // Rows of a thread's scratch column (sized for the subject's hidden depth H).
 struct Rows {
@@ -117,6 +120,7 @@ struct TrainDev {
   const uint32_t *frame_id, *px, *py;
   const float *target;
   uint32_t n_rays, S;
+  uint32_t ray_mul;       // coprime with n_rays: the order in which thread slots visit rays
   float loss_weight;      // lambda_mse
   uint64_t seed;
   float bg[3];
@@ -139,6 +143,32 @@ struct TrainDev {
   const float *grad_rgb;  // [n][3] dL/dC from the caller, or NULL (MSE against target)
   int forward_only;       // stop after compositing
 };
+
+// The ray whose samples thread slot q (of the fwd/bwd kernels) evaluates: slot q takes
+// sample q mod S of ray (q / S) ray_mul mod n_rays.  With ray_mul near 0.618 n_rays the
+// rays in flight at one time lie spread over the batch; taken in batch order they would be
+// neighbours from one image patch whose scatter-adds all hit the same table entries and
+// voxels at once.  Every ray is visited once since ray_mul is coprime with n_rays.
+__device__ __forceinline__ uint32_t ray_of(const TrainDev &T, uint32_t q) {
+  return (uint32_t)(((uint64_t)(q / T.S) * T.ray_mul) % T.n_rays);
+}
+
+// A multiplier coprime with n near the golden-ratio fraction of n (1 for n <= 2).
+static uint32_t ray_multiplier(uint32_t n) {
+  if (n <= 2) return 1;
+  auto gcd = [](uint32_t a, uint32_t b) {
+    while (b) {
+      const uint32_t t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  uint32_t m = (uint32_t)(0.6180339887498949 * (double)n);
+  if (m < 1) m = 1;
+  while (gcd(m, n) != 1) ++m;
+  return m;
+}
 
 // ----------------------------------------------------------------- rays
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
@@ -282,45 +312,49 @@ __device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in,
     atomicAdd(acc + b + lane, s0);
     atomicAdd(acc + b + lane + 32, s1);
   }
-  // A = D^T fragments of all four row tiles, one per step of 8 samples: loaded once per layer
-  uint32_t ah[4][4][4], al[4][4][4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const float *d0 = wcol + (r_d + 16 * m + g) * stride;
-    const float *d8 = d0 + 8 * stride;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int s = 8 * ks + t;
-      tf32_split(d0[s], ah[m][ks][0], al[m][ks][0]);
-      tf32_split(d8[s], ah[m][ks][1], al[m][ks][1]);
-      tf32_split(d0[s + 4], ah[m][ks][2], al[m][ks][2]);
-      tf32_split(d8[s + 4], ah[m][ks][3], al[m][ks][3]);
-    }
-  }
+  // A = D^T fragments of two row tiles at a time (one per step of 8 samples), so that the
+  // hi/lo fragments take 64 registers; H is read once per pair of row tiles
 #pragma unroll 1
-  for (int n0 = 0; n0 < n_in; n0 += 8) {
-    uint32_t bh[4][2], bl[4][2];   // B = H fragments of this column tile
-    const float *hk = wcol + (r_in + n0 + g) * stride;
+  for (int mh = 0; mh < 4; mh += 2) {
+    uint32_t ah[2][4][4], al[2][4][4];
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      tf32_split(hk[8 * ks + t], bh[ks][0], bl[ks][0]);
-      tf32_split(hk[8 * ks + t + 4], bh[ks][1], bl[ks][1]);
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int mm = 0; mm < 2; ++mm) {
+      const float *d0 = wcol + (r_d + 16 * (mh + mm) + g) * stride;
+      const float *d8 = d0 + 8 * stride;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        mma_tf32(c, al[m][ks], bh[ks]);
-        mma_tf32(c, ah[m][ks], bl[ks]);
-        mma_tf32(c, ah[m][ks], bh[ks]);
+        const int s = 8 * ks + t;
+        tf32_split(d0[s], ah[mm][ks][0], al[mm][ks][0]);
+        tf32_split(d8[s], ah[mm][ks][1], al[mm][ks][1]);
+        tf32_split(d0[s + 4], ah[mm][ks][2], al[mm][ks][2]);
+        tf32_split(d8[s + 4], ah[mm][ks][3], al[mm][ks][3]);
       }
-      // c = C[16m + g][n0 + 2t], C[16m + g][n0 + 2t + 1], C[16m + g + 8][n0 + 2t], C[16m + g + 8][n0 + 2t + 1]
-      float *o = acc + wt + (n0 + 2 * t) * kWidth + 16 * m + g;
-      atomicAdd(o, c[0]);
-      atomicAdd(o + kWidth, c[1]);
-      atomicAdd(o + 8, c[2]);
-      atomicAdd(o + kWidth + 8, c[3]);
+    }
+#pragma unroll 1
+    for (int n0 = 0; n0 < n_in; n0 += 8) {
+      uint32_t bh[4][2], bl[4][2];   // B = H fragments of this column tile
+      const float *hk = wcol + (r_in + n0 + g) * stride;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        tf32_split(hk[8 * ks + t], bh[ks][0], bl[ks][0]);
+        tf32_split(hk[8 * ks + t + 4], bh[ks][1], bl[ks][1]);
+      }
+#pragma unroll
+      for (int mm = 0; mm < 2; ++mm) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          mma_tf32(c, al[mm][ks], bh[ks]);
+          mma_tf32(c, ah[mm][ks], bl[ks]);
+          mma_tf32(c, ah[mm][ks], bh[ks]);
+        }
+        // c = C[16m + g][n0 + 2t], C[16m + g][n0 + 2t + 1], C[16m + g + 8][n0 + 2t], C[16m + g + 8][n0 + 2t + 1]
+        float *o = acc + wt + (n0 + 2 * t) * kWidth + 16 * (mh + mm) + g;
+        atomicAdd(o, c[0]);
+        atomicAdd(o + kWidth, c[1]);
+        atomicAdd(o + 8, c[2]);
+        atomicAdd(o + kWidth + 8, c[3]);
+      }
     }
   }
 }
@@ -487,7 +521,7 @@ __device__ __forceinline__ void warp_fwd(const float *__restrict__ Wt, int rs, f
 // kernel: per-sample gathers (LBS warp, PE, hash encoding) one sample per thread, both MLPs
 // as warp-level tensor-core layers over the samples' scratch columns (float32 accuracy).
 // Writes (r, g, b, alpha) per sample slot (zero for a ray that misses the box).
-__global__ void __launch_bounds__(kBwdThreads, 1) train_fwd_kernel(FieldParams P, TrainDev T) {
+__global__ void __launch_bounds__(kFwdThreads, 1) train_fwd_kernel(FieldParams P, TrainDev T) {
   extern __shared__ float4 smem4[];
   float *sW = reinterpret_cast<float *>(smem4);        // the weights in the padded layout T.pl
   for (int q = 0; q < T.pl.n_seg; ++q) {
@@ -511,9 +545,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_fwd_kernel(FieldParams P
   const uint32_t step = gridDim.x * blockDim.x;
   const uint32_t n_iter = (n + step - 1) / step;
   for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t j = it * step + blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t r = j < n ? j / T.S : 0;
-    const bool active = j < n && T.raycnt[r] != 0;
+    const uint32_t q = it * step + blockIdx.x * blockDim.x + threadIdx.x;   // thread slot
+    const uint32_t r = q < n ? ray_of(T, q) : 0;
+    const uint32_t j = r * T.S + q % T.S;                                       // sample slot
+    const bool active = q < n && T.raycnt[r] != 0;
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     float S = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
@@ -558,7 +593,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_fwd_kernel(FieldParams P
                                   sW + PL.chb[l - 1], nullptr, 0, true, R_CH + l * kWidth);
     warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
                            D_CL);
-    if (j < n) {
+    if (q < n) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (active) {
         const float o0 = col[D_CL * stride], o1 = col[(D_CL + 1) * stride], o2 = col[(D_CL + 2) * stride],
@@ -604,9 +639,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
   const uint32_t step = gridDim.x * blockDim.x;
   const uint32_t n_iter = (n + step - 1) / step;
   for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t j = it * step + blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t r = j < n ? j / T.S : 0;
-    bool active = j < n && T.raycnt[r] != 0;
+    const uint32_t q = it * step + blockIdx.x * blockDim.x + threadIdx.x;   // thread slot
+    const uint32_t r = q < n ? ray_of(T, q) : 0;
+    const uint32_t j = r * T.S + q % T.S;                                       // sample slot
+    bool active = q < n && T.raycnt[r] != 0;
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) g4 = __ldcs(T.out + j);
@@ -768,7 +804,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
         for (int sI = 0; sI < 32; ++sI) {
           const uint32_t jj = j0 + sI;
           if (jj >= n) break;
-          const int fr = (int)T.frame_id[jj / T.S];
+          const int fr = (int)T.frame_id[ray_of(T, jj)];
           if (fr != cur) {
             if (cur >= 0) {
               atomicAdd(accF + cur * kWidth + lane, s0);
@@ -862,7 +898,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       // dL/dG_i of each frame: dR_i += dp_i x^T, dt_i += dp_i over the warp's 32 samples;
       // lane owns 9 of the 24 x 12 entries and sums them per run of equal frames
       const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
-      const int fl = j0 + lane < n ? (int)T.frame_id[(j0 + lane) / T.S] : -1;
+      const int fl = j0 + lane < n ? (int)T.frame_id[ray_of(T, j0 + lane)] : -1;
       const int f0 = __shfl_sync(0xffffffffu, fl, 0);
       if (__all_sync(0xffffffffu, fl == f0) && f0 >= 0) {
         // one frame in the warp: C[3i + r][c] = sum_s dp_i[s][r] (x_s, y_s, z_s, 1)[c] as one
@@ -1096,7 +1132,9 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   }
   if ((r = grow(s->t_raycnt, s->tw_rays, (size_t)b->n_rays)) != NR_OK) return r;
   const Rows rows = make_rows((int)s->hidden);
-  if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * rows.total * kBwdThreads)) != NR_OK) return r;
+  if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * rows.total * std::max(kFwdThreads, kBwdThreads))) !=
+      NR_OK)
+    return r;
   const size_t n_acc = (size_t)blocks;                 // one accumulator per block
   if ((r = grow(s->t_wacc, s->tw_acc, n_acc * A)) != NR_OK) return r;
   if ((r = grow(s->t_red, s->tw_red, (size_t)A)) != NR_OK) return r;
@@ -1128,6 +1166,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.target = b->target_rgb;
   T.n_rays = b->n_rays;
   T.S = b->n_samples;
+  T.ray_mul = ray_multiplier(b->n_rays);
   T.loss_weight = b->loss_weight > 0.f ? b->loss_weight : 1.f;
   T.seed = b->step_seed;
   for (int k = 0; k < 3; ++k) T.bg[k] = b->bg[k];
@@ -1159,7 +1198,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   NR_CHECK_CUDA(cudaGetLastError());
   const size_t smem_f = sizeof(float) * T.pl.total;
   NR_CHECK_CUDA(cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
-  train_fwd_kernel<<<blocks, kBwdThreads, smem_f, st>>>(P, T);
+  train_fwd_kernel<<<blocks, kFwdThreads, smem_f, st>>>(P, T);
   NR_CHECK_CUDA(cudaGetLastError());
   train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
   NR_CHECK_CUDA(cudaGetLastError());
