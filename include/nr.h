@@ -64,7 +64,7 @@ typedef struct nr_subject nr_subject;   /* opaque, library-owned */
  *   box_min + (i, j, k) * (box_max - box_min) / (r - 1); the last channel is
  *   the background and is not a bone.
  * Hash grid (canonical encoding): hash_levels levels of 2^log2_T entries with
- *   hash_feats features each; level_res[l] is the grid resolution N_l;
+ *   hash_feats features each; level_res[l] is the grid resolution N_l (1..65536);
  *   hash_table[L][T][F] float32 initial values.
  * Canonical MLP (MLP_nerf, Sec. 4.4): mlp_in -> mlp_width (ReLU) x
  *   mlp_hidden_layers -> 4; mlp_params packs, per layer, W[out][in] row-major

@@ -216,12 +216,14 @@ struct nr_subject {
   // training workspace (grow-only)
   size_t tw_samples = 0;             // capacity of t_samp / t_out / t_T
   size_t tw_rays = 0;                // capacity of t_raycnt
+  size_t tw_live = 0;                // capacity of t_live
   size_t tw_acc = 0;                 // capacity of t_wacc (floats)
   size_t tw_red = 0, tw_scratch = 0;  // capacities of t_red, t_scratch (floats)
   float4 *t_samp = nullptr;          // [n_rays * S] x, y, z, delta
   float4 *t_out = nullptr;           // [n_rays * S] (r, g, b, alpha), then (dL/dc, dL/dalpha)
   float *t_T = nullptr;              // [n_rays * S] transmittance before each sample
   uint32_t *t_raycnt = nullptr;      // [n_rays] S if the ray meets the box, else 0
+  uint32_t *t_live = nullptr;        // [n_rays * S / 32] per 32 thread slots: which carry gradient
   float *t_scratch = nullptr;        // per-thread activation columns of the backward kernel
   float *t_wacc = nullptr;           // per-warp private MLP-gradient accumulators
   float *t_red = nullptr;            // their sum (float32 blob layout + per-frame bias rows)

@@ -614,7 +614,7 @@ static void free_subject(nr_subject *s) {
                   s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->blob,      s->tc_bf16,   s->tc_f16,
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
-                  s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_scratch, s->t_wacc,    s->t_red,
+                  s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_live,   s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
                   s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
                   s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG, s->f_omega_o,
@@ -648,7 +648,8 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   for (int k = 0; k < 3; ++k) NR_REQUIRE(d->box_max[k] > d->box_min[k], "empty box");
   for (uint32_t i = 0; i < d->n_bones; ++i)
     NR_REQUIRE(d->parents[i] < (int32_t)i && d->parents[i] >= -1, "parents[%u] must be -1 or < %u", i, i);
-  for (uint32_t l = 0; l < d->hash_levels; ++l) NR_REQUIRE(d->level_res[l] >= 1, "level_res must be >= 1");
+  for (uint32_t l = 0; l < d->hash_levels; ++l)
+    NR_REQUIRE(d->level_res[l] >= 1 && d->level_res[l] <= 65536, "level_res must be 1..65536");
 
   NR_CHECK_CUDA(cudaSetDevice(d->device));
   cudaStream_t st = (cudaStream_t)stream;

@@ -129,6 +129,7 @@ struct TrainDev {
   float4 *samp, *out;
   float *T;
   uint32_t *raycnt;
+  uint32_t *live;         // per warp of 32 thread slots: bit l set if slot l's sample has a gradient
   float *loss;
   float2 *g_table;
   float *g_wvol;
@@ -267,6 +268,37 @@ __global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
   if ((threadIdx.x & 31) == 0) atomicAdd(T.loss, lsum / (3.f * (float)T.n_rays));
 }
 
+// ------------------------------------------------------- warp-aggregated scatter-add
+// The samples of a warp lie in order along one ray, so lanes that add into the same cell
+// (hash level cell, weight-volume cell) are runs of consecutive lanes.  run_sum sums the
+// values of each run into its first lane (a segmented suffix sum over shuffles, stopping
+// once no run is longer than the distance reached) and returns whether this lane heads a
+// valid run: only head lanes issue the atomics, with the run's totals.  A run is a maximal
+// stretch of valid lanes with equal keys (key_lo, key_hi); invalid lanes are runs of their
+// own and add nothing.  Every lane of the warp must call it.
+template <int NV>
+__device__ __forceinline__ bool run_sum(uint32_t key_lo, uint32_t key_hi, bool valid, float (&v)[NV]) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t plo = __shfl_up_sync(0xffffffffu, key_lo, 1), phi = __shfl_up_sync(0xffffffffu, key_hi, 1);
+  const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+  const bool pvalid = lane > 0 && ((vmask >> (lane - 1)) & 1u);
+  const bool head = !valid || !pvalid || plo != key_lo || phi != key_hi;
+  const uint32_t heads = __ballot_sync(0xffffffffu, head);
+  const int run = __popc(heads & (0xffffffffu >> (31 - lane)));   // heads at lanes 0..lane
+#pragma unroll 1
+  for (int d = 1; d < 32; d <<= 1) {
+    const int rd = __shfl_down_sync(0xffffffffu, run, d);
+    const bool take = lane + d < 32 && rd == run;
+    if (!__any_sync(0xffffffffu, take)) break;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float o = __shfl_down_sync(0xffffffffu, v[k], d);
+      if (take) v[k] += o;
+    }
+  }
+  return head && valid;
+}
+
 // ---------------------------------------------------------------- backward
 // TF32 with an error term: x = hi + lo, both exactly representable in tf32; a product
 // x y = hi_x hi_y + hi_x lo_y + lo_x hi_y up to a term below float32's rounding, so three
@@ -296,7 +328,7 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
 // finished 16 x 8 tile is added into the block's accumulator acc[wt + k * 64 + j] with
 // fire-and-forget atomics (shared by the block's warps); acc[b + j] += sum_s d[s][j].
 // `wcol` points at the warp's column 0 (row r of sample s is wcol[r * stride + s]).
-__device__ __forceinline__ void wgrad64(const float *wcol, int stride, int r_in, int n_in, int r_d, float *acc,
+__device__ __noinline__ void wgrad64(const float *wcol, int stride, int r_in, int n_in, int r_d, float *acc,
                                         int wt, int b, bool with_bias) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   if (with_bias) {
@@ -396,7 +428,7 @@ __device__ __forceinline__ void wgrad4(const float *wcol, int stride, int r_in, 
 // delta from scratch rows r_d.., the mask from rows r_h..; the result goes to rows r_out..
 // (added to them when `accumulate`).  Every lane of the warp must take part.
 template <int OUT, int IN>
-__device__ __forceinline__ void warp_back(const float *__restrict__ Wt, int rs, float *wcol, int stride, int r_d,
+__device__ __noinline__ void warp_back(const float *__restrict__ Wt, int rs, float *wcol, int stride, int r_d,
                                           int r_h, int r_out, bool accumulate) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   constexpr int KS = (OUT + 7) / 8, MT = IN / 16;
@@ -549,6 +581,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) train_fwd_kernel(FieldParams P
     const uint32_t r = q < n ? ray_of(T, q) : 0;
     const uint32_t j = r * T.S + q % T.S;                                       // sample slot
     const bool active = q < n && T.raycnt[r] != 0;
+    if (!__any_sync(0xffffffffu, active)) {   // 32 slots of rays that miss the box
+      if (q < n) T.out[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((threadIdx.x & 31) == 0 && q < n) T.live[q >> 5] = 0u;
+      continue;
+    }
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     float S = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
@@ -593,6 +630,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) train_fwd_kernel(FieldParams P
                                   sW + PL.chb[l - 1], nullptr, 0, true, R_CH + l * kWidth);
     warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
                            D_CL);
+    {
+      // the slots whose samples carry a gradient (in the box, warped into the canonical box);
+      // the backward skips the others, which add exactly zero
+      const uint32_t lw = __ballot_sync(0xffffffffu, active && inside);
+      if ((threadIdx.x & 31) == 0 && q < n) T.live[q >> 5] = lw;
+    }
     if (q < n) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (active) {
@@ -642,7 +685,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     const uint32_t q = it * step + blockIdx.x * blockDim.x + threadIdx.x;   // thread slot
     const uint32_t r = q < n ? ray_of(T, q) : 0;
     const uint32_t j = r * T.S + q % T.S;                                       // sample slot
-    bool active = q < n && T.raycnt[r] != 0;
+    // the forward's mask: a slot outside it (no box hit, or warped out of the canonical box)
+    // adds exactly zero to every gradient, and a warp without live slots has nothing to do
+    const uint32_t lw = q - lane < n ? T.live[(q - lane) >> 5] : 0u;
+    if (lw == 0u) continue;
+    bool active = (lw >> lane) & 1u;
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) g4 = __ldcs(T.out + j);
@@ -734,44 +781,55 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     }
     __syncwarp();
     float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
-    if (active) {
-      // ---------------- hash backward: scatter-add and dL/dx_final
-        {
-          const float p0 = (xf0 - P.bmin[0]) * P.inv_box[0];
-          const float p1 = (xf1 - P.bmin[1]) * P.inv_box[1];
-          const float p2 = (xf2 - P.bmin[2]) * P.inv_box[2];
-          for (int l = 0; l < P.L; ++l) {
-            const float da = col[(R_DENC + 2 * l) * stride], db = col[(R_DENC + 2 * l + 1) * stride];
-            const uint32_t N = P.level_res[l];
-            const float fn = (float)N;
-            const float q0 = p0 * fn, q1 = p1 * fn, q2 = p2 * fn;
-            const float a0 = fminf(floorf(q0), fn - 1.f), a1 = fminf(floorf(q1), fn - 1.f),
-                        a2 = fminf(floorf(q2), fn - 1.f);
-            const float fr[3] = {q0 - a0, q1 - a1, q2 - a2};
-            HashCell c;
-            hash_cell(P, l, p0, p1, p2, c);
-            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+    {
+      // ---------------- hash backward: warp-aggregated scatter-add and dL/dx_final
+      const float p0 = active ? (xf0 - P.bmin[0]) * P.inv_box[0] : 0.f;
+      const float p1 = active ? (xf1 - P.bmin[1]) * P.inv_box[1] : 0.f;
+      const float p2 = active ? (xf2 - P.bmin[2]) * P.inv_box[2] : 0.f;
+      for (int l = 0; l < P.L; ++l) {
+        const float da = active ? col[(R_DENC + 2 * l) * stride] : 0.f;
+        const float db = active ? col[(R_DENC + 2 * l + 1) * stride] : 0.f;
+        const uint32_t N = P.level_res[l];
+        const float fn = (float)N;
+        const float q0 = p0 * fn, q1 = p1 * fn, q2 = p2 * fn;
+        const float a0 = fminf(floorf(q0), fn - 1.f), a1 = fminf(floorf(q1), fn - 1.f),
+                    a2 = fminf(floorf(q2), fn - 1.f);
+        const float fr[3] = {q0 - a0, q1 - a1, q2 - a2};
+        HashCell c;
+        hash_cell(P, l, p0, p1, p2, c);
+        float v[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const size_t off = (size_t)l * (P.T_mask + 1) + c.idx[k];
-              atomicAdd(T.g_table + off, make_float2(c.w[k] * da, c.w[k] * db));
-              const float2 v = __ldg(P.table32 + off);
-              const float sv = v.x * da + v.y * db;
-              const float wx = (k & 1) ? fr[0] : 1.f - fr[0], wy = ((k >> 1) & 1) ? fr[1] : 1.f - fr[1],
-                          wz = (k >> 2) ? fr[2] : 1.f - fr[2];
-              const float sx = (k & 1) ? 1.f : -1.f, sy = ((k >> 1) & 1) ? 1.f : -1.f, sz = (k >> 2) ? 1.f : -1.f;
-              gp0 = fmaf(sv, sx * wy * wz, gp0);
-              gp1 = fmaf(sv, wx * sy * wz, gp1);
-              gp2 = fmaf(sv, wx * wy * sz, gp2);
-            }
-            dx0 = fmaf(gp0, fn, dx0);
-            dx1 = fmaf(gp1, fn, dx1);
-            dx2 = fmaf(gp2, fn, dx2);
-          }
-          dx0 *= P.inv_box[0];
-          dx1 *= P.inv_box[1];
-          dx2 *= P.inv_box[2];
+        for (int k = 0; k < 8; ++k) {
+          v[2 * k] = c.w[k] * da;
+          v[2 * k + 1] = c.w[k] * db;
         }
+        const uint32_t ka = (uint32_t)a0 | ((uint32_t)a1 << 16), kb = (uint32_t)a2;
+        if (run_sum<16>(ka, kb, active, v)) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            atomicAdd(T.g_table + (size_t)l * (P.T_mask + 1) + c.idx[k], make_float2(v[2 * k], v[2 * k + 1]));
+        }
+        if (active) {
+          float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float2 tv = __ldg(P.table32 + (size_t)l * (P.T_mask + 1) + c.idx[k]);
+            const float sv = tv.x * da + tv.y * db;
+            const float wx = (k & 1) ? fr[0] : 1.f - fr[0], wy = ((k >> 1) & 1) ? fr[1] : 1.f - fr[1],
+                        wz = (k >> 2) ? fr[2] : 1.f - fr[2];
+            const float sx = (k & 1) ? 1.f : -1.f, sy = ((k >> 1) & 1) ? 1.f : -1.f, sz = (k >> 2) ? 1.f : -1.f;
+            gp0 = fmaf(sv, sx * wy * wz, gp0);
+            gp1 = fmaf(sv, wx * sy * wz, gp1);
+            gp2 = fmaf(sv, wx * wy * sz, gp2);
+          }
+          dx0 = fmaf(gp0, fn, dx0);
+          dx1 = fmaf(gp1, fn, dx1);
+          dx2 = fmaf(gp2, fn, dx2);
+        }
+      }
+      dx0 *= P.inv_box[0];
+      dx1 *= P.inv_box[1];
+      dx2 *= P.inv_box[2];
     }
     float ds0 = dx0, ds1 = dx1, ds2 = dx2;
     if (P.res_enabled) {
@@ -843,53 +901,62 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
           ds2 += dh[2] * P.box_ih[2];
       }
     }
-    if (active) {
-        // ---------------- inverse-LBS backward: scatter into the weight volume
-        // and, for the pose refiner, dL/dp_i of each candidate p_i = G_i x:
-        //   x_skel = sum_i w_i p_i / D,  w_i = W_i(p_i)
-        //   dL/dp_i = (w_i / D) dL/dx_skel + dL/dw_i grad W_i(p_i)
-        {
-          const float D = fmaxf(S, kEpsW);
-          const float m = S > kEpsW ? 1.f : 0.f;
-          const int R = P.wres, R3 = R * R * R;
-          const size_t QC = quad_channel(R);
-          if (T.dG) {
-            col[(R_XS + 0) * stride] = s.x;
-            col[(R_XS + 1) * stride] = s.y;
-            col[(R_XS + 2) * stride] = s.z;
-          }
-          for (int i = 0; i < kBones; ++i) {
-            const float *g = G + 12 * i;
-            const float p0 = fmaf(g[0], s.x, fmaf(g[1], s.y, fmaf(g[2], s.z, g[3])));
-            const float p1 = fmaf(g[4], s.x, fmaf(g[5], s.y, fmaf(g[6], s.z, g[7])));
-            const float p2 = fmaf(g[8], s.x, fmaf(g[9], s.y, fmaf(g[10], s.z, g[11])));
-            const float dw = (ds0 * (p0 - m * xs0) + ds1 * (p1 - m * xs1) + ds2 * (p2 - m * xs2)) / D + dS_alpha;
-            const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
-            const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
-            const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
-            if (T.dG) {
-              float gx, gy, gz;
-              const float w = trilinear_quad_grad(P.wquad + (size_t)i * QC, R, ux, uy, uz, gx, gy, gz);
-              const float a = w / D;
-              col[(R_DP + 3 * i + 0) * stride] = fmaf(a, ds0, dw * gx * P.vol_scale[0]);
-              col[(R_DP + 3 * i + 1) * stride] = fmaf(a, ds1, dw * gy * P.vol_scale[1]);
-              col[(R_DP + 3 * i + 2) * stride] = fmaf(a, ds2, dw * gz * P.vol_scale[2]);
-            }
-            if (dw == 0.f) continue;
-            const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
-            const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
-            if (ix < -1 || iy < -1 || iz < -1 || ix >= R || iy >= R || iz >= R) continue;
-            const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
-            float *chg = T.g_wvol + (size_t)i * R3;
+    {
+      // ---------------- inverse-LBS backward: warp-aggregated scatter into the weight volume
+      // and, for the pose refiner, dL/dp_i of each candidate p_i = G_i x:
+      //   x_skel = sum_i w_i p_i / D,  w_i = W_i(p_i)
+      //   dL/dp_i = (w_i / D) dL/dx_skel + dL/dw_i grad W_i(p_i)
+      const float D = fmaxf(S, kEpsW);
+      // one division per sample: a per-bone quotient with a vanishing numerator (far from the
+      // body S, and with it the gradient reaching x_skel, goes to zero) takes the division's
+      // slow path 24 times a sample
+      const float inv_D = 1.f / D;
+      const float m = S > kEpsW ? 1.f : 0.f;
+      const int R = P.wres, R3 = R * R * R;
+      const size_t QC = quad_channel(R);
+      if (T.dG && active) {
+        col[(R_XS + 0) * stride] = s.x;
+        col[(R_XS + 1) * stride] = s.y;
+        col[(R_XS + 2) * stride] = s.z;
+      }
+      for (int i = 0; i < kBones; ++i) {
+        const float *g = G + 12 * i;
+        const float p0 = fmaf(g[0], s.x, fmaf(g[1], s.y, fmaf(g[2], s.z, g[3])));
+        const float p1 = fmaf(g[4], s.x, fmaf(g[5], s.y, fmaf(g[6], s.z, g[7])));
+        const float p2 = fmaf(g[8], s.x, fmaf(g[9], s.y, fmaf(g[10], s.z, g[11])));
+        const float dw = (ds0 * (p0 - m * xs0) + ds1 * (p1 - m * xs1) + ds2 * (p2 - m * xs2)) * inv_D + dS_alpha;
+        const float ux = (p0 - P.bmin[0]) * P.vol_scale[0];
+        const float uy = (p1 - P.bmin[1]) * P.vol_scale[1];
+        const float uz = (p2 - P.bmin[2]) * P.vol_scale[2];
+        if (T.dG && active) {
+          float gx, gy, gz;
+          const float w = trilinear_quad_grad(P.wquad + (size_t)i * QC, R, ux, uy, uz, gx, gy, gz);
+          const float a = w * inv_D;
+          col[(R_DP + 3 * i + 0) * stride] = fmaf(a, ds0, dw * gx * P.vol_scale[0]);
+          col[(R_DP + 3 * i + 1) * stride] = fmaf(a, ds1, dw * gy * P.vol_scale[1]);
+          col[(R_DP + 3 * i + 2) * stride] = fmaf(a, ds2, dw * gz * P.vol_scale[2]);
+        }
+        const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
+        const bool in_range = fx0 >= -1.f && fy0 >= -1.f && fz0 >= -1.f && fx0 < (float)R && fy0 < (float)R &&
+                              fz0 < (float)R;
+        const bool valid = active && dw != 0.f && in_range;
+        const int ix = valid ? (int)fx0 : 0, iy = valid ? (int)fy0 : 0, iz = valid ? (int)fz0 : 0;
+        const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
+        float v[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int ax = ix + (c & 1), ay = iy + ((c >> 1) & 1), az = iz + (c >> 2);
-              if (ax < 0 || ay < 0 || az < 0 || ax >= R || ay >= R || az >= R) continue;
-              const float w = ((c & 1) ? fx : 1.f - fx) * (((c >> 1) & 1) ? fy : 1.f - fy) * ((c >> 2) ? fz : 1.f - fz);
-              atomicAdd(chg + (az * R + ay) * R + ax, dw * w);
-            }
+        for (int c = 0; c < 8; ++c)
+          v[c] = dw * (((c & 1) ? fx : 1.f - fx) * (((c >> 1) & 1) ? fy : 1.f - fy) * ((c >> 2) ? fz : 1.f - fz));
+        const uint32_t key = (uint32_t)(ix + 1) | ((uint32_t)(iy + 1) << 10) | ((uint32_t)(iz + 1) << 20);
+        if (run_sum<8>(key, 0u, valid, v)) {
+          float *chg = T.g_wvol + (size_t)i * R3;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int ax = ix + (c & 1), ay = iy + ((c >> 1) & 1), az = iz + (c >> 2);
+            if (ax < 0 || ay < 0 || az < 0 || ax >= R || ay >= R || az >= R) continue;
+            atomicAdd(chg + (az * R + ay) * R + ax, v[c]);
           }
         }
+      }
     }
     if (T.dG && !active)   // the refiner's reduction reads these rows of every lane
       for (int q = 0; q < 3 * kBones + 3; ++q) col[(R_DP + q) * stride] = 0.f;
@@ -1131,6 +1198,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
     s->tw_samples = n;
   }
   if ((r = grow(s->t_raycnt, s->tw_rays, (size_t)b->n_rays)) != NR_OK) return r;
+  if ((r = grow(s->t_live, s->tw_live, ((size_t)b->n_rays * b->n_samples + 31) / 32)) != NR_OK) return r;
   const Rows rows = make_rows((int)s->hidden);
   if ((r = grow(s->t_scratch, s->tw_scratch, (size_t)blocks * rows.total * std::max(kFwdThreads, kBwdThreads))) !=
       NR_OK)
@@ -1178,6 +1246,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   T.out = s->t_out;
   T.T = s->t_T;
   T.raycnt = s->t_raycnt;
+  T.live = s->t_live;
   T.loss = s->loss_acc;
   T.g_table = reinterpret_cast<float2 *>(s->g_table);
   T.g_wvol = s->g_wvol;
