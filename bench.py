@@ -445,8 +445,8 @@ def run_reference(a):
 
 # DRAM bytes (read + write) of the field kernel's launches for one frame of the frame workload,
 # from one ncu capture of the sources whose SHA-256 is given (profiles/field_tc_bf16_frame512.md).
-FIELD_TRAFFIC = {"sha256": "0730f954b3feb5d20f908898f7beccb86cf3637da096fd1ffc6a16f9583d608b",
-                 "bytes_per_frame": 151476736 + 43174656}
+FIELD_TRAFFIC = {"sha256": "64d60f67b9cfa98d8f8fcf4b8aa0f9f8482b933405330af892aba6490f18f48c",
+                 "bytes_per_frame": 151567616 + 43050752}
 FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 

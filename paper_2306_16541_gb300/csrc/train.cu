@@ -17,9 +17,12 @@
 //     (fire-and-forget atomics shared by the block's warps); one kernel sums
 //     the block accumulators at the end;
 //   * hash-table and weight-volume gradients are scattered with float2 /
-//     float atomics straight into the gradient buffers;
+//     float atomics straight into the gradient buffers, warp-aggregated: the
+//     lanes of a run that adds into one cell sum first (run_sum);
 //   * thread slots visit the batch's rays in a scattered order (ray_of), so
-//     that the rays in flight together do not come from one image patch.
+//     that the rays in flight together do not come from one image patch;
+//   * the forward records which slots carry a gradient (live mask); the
+//     backward skips the rest.
 #include <math.h>
 #include <string.h>
 
