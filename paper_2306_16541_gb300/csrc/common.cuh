@@ -80,6 +80,11 @@ struct FieldParams {
   uint32_t level_res[kMaxLevels];
   const float2 *table32;             // [L][T] float2
   const __half2 *table16;            // [L][T] half2
+  // dense levels of the f16 table as corner blocks: entry (x, y, z) of level l, at
+  // dq_off[l] + (z N + y) N + x for x, y < N and z <= N, holds the half2 values of the
+  // vertices (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) on plane z (dense_quad_kernel)
+  const uint4 *dense_quad;
+  uint32_t dq_off[kMaxLevels];
   int use_f16_table;
   int hidden;                        // canonical hidden layers
   int res_enabled, res_freqs;
@@ -139,6 +144,9 @@ struct nr_subject {
   uint32_t adam_t = 0;
   // derived, rebuilt when parameters change
   __half2 *table16 = nullptr;
+  uint4 *dense_quad = nullptr;       // corner blocks of the dense levels of table16 (or NULL)
+  size_t n_dq = 0;                   // its entries
+  uint32_t dq_off[nr::kMaxLevels] = {};  // per dense level: first entry
   float *blob = nullptr;
   float4 *wquad = nullptr;           // corner-block copy of the bone channels of wvol
   float *bone_box = nullptr;         // [24][6] support boxes of the bone channels (render skip)

@@ -189,6 +189,28 @@ __device__ __forceinline__ float2 table_read(const FieldParams &P, int l, uint32
 // trilinearly from the f16 or f32 table (the dtype test sits outside the corners).
 __device__ __forceinline__ void hash_level(const FieldParams &P, int l, float p0, float p1, float p2, float &fa,
                                            float &fb) {
+  if (P.use_f16_table && P.dense_quad && ((P.dense_mask >> l) & 1u)) {
+    // a dense level from its corner blocks: the same eight values, weights and order of
+    // accumulation as the per-corner reads below, in two 16-byte loads
+    const uint32_t N = P.level_res[l];
+    const float fn = (float)N;
+    const float q0 = p0 * fn, q1 = p1 * fn, q2 = p2 * fn;
+    const float a0 = fminf(floorf(q0), fn - 1.f), a1 = fminf(floorf(q1), fn - 1.f), a2 = fminf(floorf(q2), fn - 1.f);
+    const float f0 = q0 - a0, f1 = q1 - a1, f2 = q2 - a2;
+    const uint4 *Q = P.dense_quad + P.dq_off[l] + ((size_t)a2 * N + (uint32_t)a1) * N + (uint32_t)a0;
+    const uint4 lo = __ldg(Q), hi = __ldg(Q + (size_t)N * N);
+    const uint32_t u[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    fa = 0.f;
+    fb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = ((k & 1) ? f0 : 1.f - f0) * (((k >> 1) & 1) ? f1 : 1.f - f1) * ((k >> 2) ? f2 : 1.f - f2);
+      const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&u[k]));
+      fa = fmaf(w, v.x, fa);
+      fb = fmaf(w, v.y, fb);
+    }
+    return;
+  }
   HashCell c;
   hash_cell(P, l, p0, p1, p2, c);
   fa = 0.f;

@@ -280,6 +280,34 @@ __global__ void table_to_f16_kernel(const float2 *__restrict__ src, size_t n, __
     dst[i] = __floats2half2_rn(src[i].x, src[i].y);
 }
 
+// Corner blocks of the dense levels of the f16 table: entry (x, y, z) of level l holds the
+// vertices (x, y, z), (x + 1, y, z), (x, y + 1, z), (x + 1, y + 1, z) (row-major vertex index
+// x + y (N + 1) + z (N + 1)^2), so that a sample reads its eight corners as two 16-byte loads.
+struct DenseQuadArgs {
+  int n_levels;
+  uint32_t level[kMaxLevels], N[kMaxLevels];
+  size_t off[kMaxLevels + 1];
+  size_t T;
+};
+
+__global__ void dense_quad_kernel(const __half2 *__restrict__ t16, DenseQuadArgs a, uint4 *__restrict__ dq) {
+  const size_t n = a.off[a.n_levels];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < a.n_levels && e >= a.off[k + 1]) ++k;
+    const size_t N = a.N[k], M = N + 1, q = e - a.off[k];
+    const size_t x = q % N, y = (q / N) % N, z = q / (N * N);
+    const __half2 *t = t16 + (size_t)a.level[k] * a.T;
+    const size_t v = x + y * M + z * M * M;
+    uint4 r;
+    r.x = *reinterpret_cast<const uint32_t *>(t + v);
+    r.y = *reinterpret_cast<const uint32_t *>(t + v + 1);
+    r.z = *reinterpret_cast<const uint32_t *>(t + v + M);
+    r.w = *reinterpret_cast<const uint32_t *>(t + v + M + 1);
+    dq[e] = r;
+  }
+}
+
 // bias1[f][j] = b1[j] + sum_m W1[j][g + m] * omega[f][m]: the joint angles of
 // Omega^o enter the residual MLP's first layer (Fig. S3) as a per-pose bias.
 __global__ void fold_pose_bias_kernel(const float *__restrict__ res, int g, int pose_dim,
@@ -455,6 +483,21 @@ nr_status prepare_params(nr_subject *s, cudaStream_t st) {
   launched += pack_tc_all<__half>(s, m, st, s->tc_f16);
   // half-precision hash table, corner-block weight volume
   table_to_f16_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->table), s->n_table / 2, s->table16);
+  if (s->dense_quad) {
+    DenseQuadArgs a{};
+    for (uint32_t l = 0; l < s->L; ++l) {
+      const double n1 = (double)s->level_res[l] + 1.0;
+      if (n1 * n1 * n1 > (double)s->T) continue;
+      a.level[a.n_levels] = l;
+      a.N[a.n_levels] = s->level_res[l];
+      a.off[a.n_levels] = s->dq_off[l];
+      ++a.n_levels;
+    }
+    a.off[a.n_levels] = s->n_dq;
+    a.T = s->T;
+    dense_quad_kernel<<<1024, 256, 0, st>>>(s->table16, a, s->dense_quad);
+    ++launched;
+  }
   build_quad_kernel<<<2048, 256, 0, st>>>(s->wvol, (int)s->wres, s->wquad);
   bone_box_init_kernel<<<1, kBones * 6, 0, st>>>(s->bone_ibox, (int)s->wres);
   bone_box_kernel<<<nblk((long)kBones * s->wres * s->wres * s->wres, 256), 256, 0, st>>>(s->wvol, (int)s->wres,
@@ -574,6 +617,8 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   }
   P.table32 = reinterpret_cast<const float2 *>(s->table);
   P.table16 = s->table16;
+  P.dense_quad = s->dense_quad;
+  for (uint32_t l = 0; l < s->L; ++l) P.dq_off[l] = s->dq_off[l];
   P.use_f16_table = (o && o->feat_dtype == NR_F16) ? 1 : 0;
   P.hidden = (int)s->hidden;
   P.res_enabled = (int)s->res_enabled;
@@ -611,7 +656,7 @@ extern "C" uint64_t nr_launch_count(void) { return nr::g_launches.load(std::memo
 
 static void free_subject(nr_subject *s) {
   void *bufs[] = {s->wquad,  s->wvol,   s->g_wvol,  s->table,    s->g_table,  s->mlp,       s->g_mlp,     s->res,
-                  s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->blob,      s->tc_bf16,   s->tc_f16,
+                  s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->dense_quad, s->blob,      s->tc_bf16,   s->tc_f16,
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_live,   s->t_scratch, s->t_wacc,    s->t_red,
@@ -708,6 +753,14 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->res, s->n_res * 4);
   ALLOC(s->g_res, s->n_res * 4);
   ALLOC(s->table16, s->n_table * 2);
+  for (uint32_t l = 0; l < s->L; ++l) {   // corner blocks of the dense levels: N x N x (N + 1) each
+    const double n1 = (double)s->level_res[l] + 1.0;
+    if (n1 * n1 * n1 > (double)s->T) continue;
+    const size_t N = s->level_res[l];
+    s->dq_off[l] = (uint32_t)s->n_dq;
+    s->n_dq += N * N * (N + 1);
+  }
+  if (s->n_dq) ALLOC(s->dense_quad, s->n_dq * sizeof(uint4));
   ALLOC(s->blob, (size_t)s->lay.total * 4);
   ALLOC(s->wquad, quad_channel((int)s->wres) * kBones * sizeof(float4));
   ALLOC(s->bone_box, kBones * 6 * sizeof(float));

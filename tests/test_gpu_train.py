@@ -130,6 +130,25 @@ def test_weight_volume_gradient_on_a_kink_free_field():
         assert _rel(grads[g], ref[g]) <= 1e-4, (g, _rel(grads[g], ref[g]))
 
 
+def test_aggregated_scatter_adds_over_whole_warp_runs():
+    """128 samples per ray put each warp on 32 consecutive samples of one ray, and the
+    0.5 m cells of a resolution-4 level hold runs of up to 32 lanes: the warp-aggregated
+    scatter-adds (run sums over shuffles, one atomic per run) against the oracle, tightly,
+    on the kink-free field."""
+    subj = _linear_table(synth.subject(35, hash_scale=0.5))
+    frames = synth.training_frames(36, 2, res=32)
+    for c in frames["cameras"]:
+        c.n_samples = 128
+    batch = synth.pixel_batch(37, 48, 2, 32, 32)
+    tgt = np.random.default_rng(38).uniform(0, 1, size=(48, 3)).astype(np.float32)
+    loss, grads, _, _ = _gpu_step(subj, frames, batch, tgt, 128, 79, grad_only=True)
+    ref_loss, ref = _oracle_grads(subj, frames, batch, tgt, 128, 79)
+    assert abs(loss - ref_loss) <= 1e-5 * max(1.0, ref_loss)
+    for g in ("wvol", "table", "mlp"):
+        assert np.linalg.norm(ref[g]) > 0, g
+        assert _rel(grads[g], ref[g]) <= 1e-4, (g, _rel(grads[g], ref[g]))
+
+
 def test_gradients_with_hann_window_and_more_samples():
     subj, frames, batch, tgt = _setup(n_rays=200, n_frames=2, S=40, seed=41)
     nr = nrmod()
