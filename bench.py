@@ -30,6 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "rays/sec (512x512 frame render, 128 samples/ray, occupancy + ERT)"
+# The paper's own speed figures (one RTX 3080 Ti, ZJU-MoCap; Table 1, Table 2, Sec. 5): context
+# only, on other hardware and other data, never a ratio target.
+PAPER_CONTEXT = {
+    "hardware": "RTX 3080 Ti (Ampere), tiny-cuda-nn fp16 MLPs",
+    "inference": "1.209 frames/s at 1024x1024 (at most ~1.27 M rays/s), +213 % over HumanNeRF",
+    "training": "3.92 h for 150K iterations of 2400 rays (~94 ms per iteration), -44.5 % against HumanNeRF",
+}
 UNIT = "rays/s"
 L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
 
@@ -369,9 +376,10 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
 
 def sweep_bench(nr, device, n_oracle_pixels=384):
     """Precision sweep: 1920x1080, 192 samples per ray, the tiny workload's field with 2^20
-    entries per level (and a textured variant), no occupancy.  Every MLP tier (f32, bf16, f16,
-    fp8) x hash-feature tier (f32, f16): rays/s (CUDA events), PSNR and max-abs against the FP64
-    oracle on sampled pixels, and PSNR against the f32 GPU image."""
+    entries per level (and a textured variant), no occupancy.  Every MLP tier (f32 on CUDA
+    cores, f32_tc = float32 accuracy on the tensor cores, bf16, f16, fp8) x hash-feature tier
+    (f32, f16): rays/s (CUDA events), PSNR and max-abs against the FP64 oracle on sampled
+    pixels, and PSNR against the f32 GPU image."""
     import torch
     from oracle import field as OF
     from oracle import render as OR
@@ -393,9 +401,9 @@ def sweep_bench(nr, device, n_oracle_pixels=384):
         img = torch.empty(cam.height, cam.width, 4, device="cuda")
         base = None
         rows = []
-        for mlp in ("f32", "bf16", "f16", "fp8"):
+        for mlp in ("f32", "f32_tc", "bf16", "f16", "fp8"):
             for feat in ("f32", "f16"):
-                opts = nr.make_opts(mlp, feat, False, 0.0)
+                opts = nr.make_opts("f32" if mlp == "f32_tc" else mlp, feat, False, 0.0, f32_tc=mlp == "f32_tc")
                 S.render(cam, opts, img)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -445,8 +453,8 @@ def run_reference(a):
 
 # DRAM bytes (read + write) of the field kernel's launches for one frame of the frame workload,
 # from one ncu capture of the sources whose SHA-256 is given (profiles/field_tc_bf16_frame512.md).
-FIELD_TRAFFIC = {"sha256": "64d60f67b9cfa98d8f8fcf4b8aa0f9f8482b933405330af892aba6490f18f48c",
-                 "bytes_per_frame": 151567616 + 43050752}
+FIELD_TRAFFIC = {"sha256": "1426894afed072136a61070833752d48401fe2c1fbe22338797650bcd3200d4d",
+                 "bytes_per_frame": 152441088 + 43357696}
 FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 
@@ -590,6 +598,7 @@ def run_ours(a):
         "precision_sweep": sweep,
         "gpu_launches": launches,
         "clocks": clk,
+        "paper_context": PAPER_CONTEXT,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, poses, a.cpu_pixels)

@@ -190,7 +190,7 @@ typedef struct {
   float t_min;             /* early ray termination once transmittance < t_min; 0 = off */
   float hann_alpha;        /* residual PE window position; < 0 = all bands */
   uint32_t flags;          /* NR_RENDER_PROFILE | NR_RENDER_TCGEN05 | NR_RENDER_MMA2 |
-                              NR_RENDER_ALL_BONES, or 0 */
+                              NR_RENDER_ALL_BONES | NR_RENDER_F32_TC, or 0 */
 } nr_render_opts;
 
 /* Renders the current pose from `cam` into out_rgba[height][width][4]
@@ -400,11 +400,18 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
 #define NR_RENDER_TCGEN05 2u  /* nr_render_opts.flags: bf16/f16 MLPs on tcgen05.mma with TMEM
                                  accumulators (M = 128 tiles) instead of warp-level mma.sync */
 #define NR_RENDER_MMA2 4u     /* nr_render_opts.flags: warp-level mma.sync over two 16-row tiles per
-                                 weight-fragment read (12 warps/SM instead of 16) */
+                                 weight-fragment read (12 warps/SM instead of 20) */
 #define NR_RENDER_ALL_BONES 8u /* nr_render_opts.flags: evaluate all 24 bone channels at every sample.
                                  By default a candidate G_i x is skipped when its trilinear cell lies
                                  outside the index box of channel i's vertices above 1e-7 (weights
                                  that small change S by at most 2.4e-6); training never skips. */
+#define NR_RENDER_F32_TC 16u  /* nr_render_opts.flags with mlp_dtype NR_F32 (nr_render, nr_query):
+                                 both MLPs as warp-level tensor-core layers at float32 accuracy
+                                 (each product as three TF32 products of hi/lo parts) instead of
+                                 CUDA-core FMAs.  The first such call allocates a scratch buffer of
+                                 one 212-float column per thread of one 512-thread block per SM
+                                 (66 MB on 152 SMs); nr_render_static refuses the flag
+                                 (NR_EUNSUPPORTED).  Ignored for the other dtypes. */
 
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,

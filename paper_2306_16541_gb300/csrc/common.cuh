@@ -105,6 +105,7 @@ struct FieldParams {
   float occ_tau;                     // density threshold
   float occ_smin;                    // least bone-weight sum S of a posed cell
   const uint32_t *canon_bits;        // canonical bitfield read by kModePose
+  float *tf32_scratch;               // activation columns of the float32 tensor-core tier (or NULL)
 };
 
 struct Frame {                       // a training frame's camera (decoded)
@@ -145,6 +146,8 @@ struct nr_subject {
   // derived, rebuilt when parameters change
   __half2 *table16 = nullptr;
   uint4 *dense_quad = nullptr;       // corner blocks of the dense levels of table16 (or NULL)
+  float *r_scratch = nullptr;        // activation columns of the float32 tensor-core tier
+  size_t rw_scratch = 0;             // its capacity (floats)
   size_t n_dq = 0;                   // its entries
   uint32_t dq_off[nr::kMaxLevels] = {};  // per dense level: first entry
   float *blob = nullptr;

@@ -400,6 +400,7 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
     set_error("mlp_dtype %d is not implemented", (int)mlp_dtype);
     return NR_EUNSUPPORTED;
   }
+  if (mma_path == 3) return launch_field_tf32(P, mode, in, n_fixed, n_dev, out, device, st);
   const size_t smem = field_f32_smem(P);
   const int blocks = num_sms(device);
   if (mode == kModeRender) {
@@ -412,6 +413,25 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
     field_f32_kernel<kModeQuery><<<blocks, kF32Threads, smem, st>>>(P, in, n_fixed, n_dev, out);
   }
   NR_CHECK_CUDA(cudaGetLastError());
+  return NR_OK;
+}
+
+// The field kernel a render or query takes: 1 tcgen05, 2 two m-tiles per weight read, 3 the
+// float32 tier on the tensor cores, 0 the default of the MLP dtype.
+static int render_path(const nr_render_opts *o) {
+  if (o->mlp_dtype == NR_F32) return (o->flags & NR_RENDER_F32_TC) ? 3 : 0;
+  return (o->flags & NR_RENDER_TCGEN05) ? 1 : ((o->flags & NR_RENDER_MMA2) ? 2 : 0);
+}
+
+// One column of kTf32Rows floats per thread of one block per SM (allocated on first use).
+static nr_status grow_tf32_scratch(nr_subject *s) {
+  const size_t need = (size_t)num_sms(s->device) * kTf32Rows * kTf32Threads;
+  if (need <= s->rw_scratch) return NR_OK;
+  if (s->r_scratch) NR_CHECK_CUDA(cudaFree(s->r_scratch));
+  s->r_scratch = nullptr;
+  s->rw_scratch = 0;
+  NR_CHECK_CUDA(cudaMalloc((void **)&s->r_scratch, need * sizeof(float)));
+  s->rw_scratch = need;
   return NR_OK;
 }
 
@@ -589,8 +609,9 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
-  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
+  const int path = render_path(opts);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
+  if (path == 3 && (r = grow_tf32_scratch(s)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const uint32_t n_rays = cam->width * cam->height;
   // chunk the rays so that the worst-case sample queue of a round stays below 2^26 entries
@@ -694,8 +715,9 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   if ((r = ensure_pose(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
-  const int path = (opts->flags & NR_RENDER_TCGEN05) ? 1 : ((opts->flags & NR_RENDER_MMA2) ? 2 : 0);
+  const int path = render_path(opts);
   if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
+  if (path == 3 && (r = grow_tf32_scratch(s)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   count_launches(1);
   return launch_field(P, opts->mlp_dtype, kModeQuery, reinterpret_cast<const float4 *>(x_obs), n, nullptr, out,

@@ -116,7 +116,8 @@ CamParams cam_params(const nr_camera *c);
 int num_sms(int device);
 size_t field_f32_smem(const FieldParams &P);
 // mma_path for the bf16/f16 tiers: 0 = warp-level mma.sync over one 16-row m-tile per weight-fragment
-// read (16 warps/SM), 1 = tcgen05 (TMEM accumulators), 2 = mma.sync over two m-tiles per read (12 warps/SM).
+// read (20 warps/SM), 1 = tcgen05 (TMEM accumulators), 2 = mma.sync over two m-tiles per read (12 warps/SM);
+// for the f32 tier: 3 = TF32 tensor-core layers at float32 accuracy (field_tf32.cu), else CUDA cores.
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path = 0);
 nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
@@ -126,5 +127,10 @@ nr_status launch_field_t5(const FieldParams &P, nr_dtype mlp_dtype, int mode, co
 nr_status launch_field_tc(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mt);
 nr_status fold_frame_biases(nr_subject *s, cudaStream_t st);
+// the float32 tier on the tensor cores: threads per block and scratch rows per thread
+constexpr int kTf32Threads = 512;
+constexpr int kTf32Rows = kResGammaPad + 2 * kWidth + kMlpIn + 4;
+nr_status launch_field_tf32(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
+                            float *out, int device, cudaStream_t st);
 
 }  // namespace nr

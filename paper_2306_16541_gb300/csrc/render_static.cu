@@ -71,6 +71,10 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
   NR_REQUIRE(opts->mlp_dtype == NR_F32 || opts->mlp_dtype == NR_BF16 || opts->mlp_dtype == NR_F16,
              "nr_render_static: mlp_dtype must be NR_F32, NR_BF16 or NR_F16");
   NR_REQUIRE(opts->feat_dtype == NR_F32 || opts->feat_dtype == NR_F16, "nr_render_static: bad feat_dtype");
+  if (opts->mlp_dtype == NR_F32 && (opts->flags & NR_RENDER_F32_TC)) {
+    set_error("nr_render_static: NR_RENDER_F32_TC needs a scratch buffer the static path does not allocate");
+    return NR_EUNSUPPORTED;
+  }
   NR_REQUIRE(opts->t_min >= 0.f && opts->t_min < 1.f, "nr_render_static: t_min must be in [0, 1)");
   NR_REQUIRE(!opts->use_occupancy || s->occ_source != kOccNone, "nr_render_static: the subject has no occupancy");
   NR_REQUIRE(cam->width >= 1 && cam->height >= 1 && cam->n_samples >= 1 && cam->n_samples <= 1024,

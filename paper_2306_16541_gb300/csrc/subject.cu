@@ -618,6 +618,7 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   P.table32 = reinterpret_cast<const float2 *>(s->table);
   P.table16 = s->table16;
   P.dense_quad = s->dense_quad;
+  P.tf32_scratch = s->r_scratch;
   for (uint32_t l = 0; l < s->L; ++l) P.dq_off[l] = s->dq_off[l];
   P.use_f16_table = (o && o->feat_dtype == NR_F16) ? 1 : 0;
   P.hidden = (int)s->hidden;
@@ -656,7 +657,7 @@ extern "C" uint64_t nr_launch_count(void) { return nr::g_launches.load(std::memo
 
 static void free_subject(nr_subject *s) {
   void *bufs[] = {s->wquad,  s->wvol,   s->g_wvol,  s->table,    s->g_table,  s->mlp,       s->g_mlp,     s->res,
-                  s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->dense_quad, s->blob,      s->tc_bf16,   s->tc_f16,
+                  s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->dense_quad, s->r_scratch, s->blob,      s->tc_bf16,   s->tc_f16,
                   s->d_G,    s->d_omega, s->d_bias1,  s->ellip,    s->bits,      s->f_G,       s->f_omega,
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_live,   s->t_scratch, s->t_wacc,    s->t_red,

@@ -35,6 +35,7 @@ NR_RENDER_PROFILE = 1
 NR_RENDER_ALL_BONES = 8
 NR_RENDER_TCGEN05 = 2
 NR_RENDER_MMA2 = 4
+NR_RENDER_F32_TC = 16
 NR_ABI_VERSION = 1
 
 _fp = C.POINTER(C.c_float)
@@ -174,12 +175,13 @@ def make_camera(cam) -> nr_camera:
 
 def make_opts(mlp: str = "f32", feat: str = "f32", occupancy: bool = False, t_min: float = 0.0,
               hann_alpha: float = -1.0, profile: bool = False, tcgen05: bool = False,
-              mma2: bool = False, all_bones: bool = False) -> nr_render_opts:
+              mma2: bool = False, all_bones: bool = False, f32_tc: bool = False) -> nr_render_opts:
     o = nr_render_opts()
     o.mlp_dtype, o.feat_dtype = DTYPES[mlp], DTYPES[feat]
     o.use_occupancy, o.t_min, o.hann_alpha = int(bool(occupancy)), float(t_min), float(hann_alpha)
     o.flags = ((NR_RENDER_PROFILE if profile else 0) | (NR_RENDER_TCGEN05 if tcgen05 else 0)
-               | (NR_RENDER_MMA2 if mma2 else 0) | (NR_RENDER_ALL_BONES if all_bones else 0))
+               | (NR_RENDER_MMA2 if mma2 else 0) | (NR_RENDER_ALL_BONES if all_bones else 0)
+               | (NR_RENDER_F32_TC if f32_tc else 0))
     return o
 
 

@@ -381,3 +381,42 @@ def test_bone_skipping_changes_nothing_visible(mlp):
         S.close()
     assert full[..., 3].max() > 0.2
     assert np.abs(skip - full).max() <= 1e-4, np.abs(skip - full).max()
+
+
+def test_f32_tensor_core_tier(tiny_structured, frame):
+    """NR_RENDER_F32_TC: both MLPs as warp-level tensor-core layers with three TF32 products
+    per step.  Within the float32 bar of the oracle (max abs <= 1e-3) on the tiny workload and
+    on the frame workload with occupancy, within 1e-5 of the CUDA-core float32 path, query
+    rows likewise (the warp's gathers are the same code: bitwise), and refused by
+    nr_render_static, which allocates nothing."""
+    import ctypes as C
+    nr = nrmod()
+    for cfg, cam, occ in ((tiny_structured, tiny_structured["camera"], False),
+                          (frame, _small(frame["camera"], 64), True)):
+        S = nr.Subject(cfg["subject"])
+        try:
+            S.set_pose(*cfg["pose"])
+            tc = S.render(cam, nr.make_opts("f32", "f32", occ, 0.0, f32_tc=True)).cpu().numpy()
+            fm = S.render(cam, nr.make_opts("f32", "f32", occ, 0.0)).cpu().numpy()
+        finally:
+            S.close()
+        ref = oracle_render(cfg["subject"], cfg["pose"], cam, occ).reshape(tc.shape)
+        assert ref[..., 3].max() > 0.1
+        assert np.abs(tc - ref).max() <= 1e-3, np.abs(tc - ref).max()
+        assert np.abs(tc - fm).max() <= 1e-5, np.abs(tc - fm).max()
+    x = torch.from_numpy(np.random.default_rng(12).uniform(-0.9, 0.9, size=(1001, 3)).astype(np.float32)).cuda()
+    S = nr.Subject(frame["subject"])
+    try:
+        S.set_pose(*frame["pose"])
+        qa = S.query(x, nr.make_opts("f32", "f32", f32_tc=True)).cpu().numpy()
+        qb = S.query(x, nr.make_opts("f32", "f32")).cpu().numpy()
+        out = torch.empty(32, 32, 4, device="cuda")
+        cam = nr.make_camera(_small(frame["camera"], 32))
+        rc = nr.lib.nr_render_static(S.h, C.byref(cam), C.byref(nr.make_opts("f32", "f32", f32_tc=True)),
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        torch.cuda.synchronize()
+    finally:
+        S.close()
+    assert rc == nr.NR_EUNSUPPORTED
+    assert np.array_equal(qa[:, :4], qb[:, :4])
+    assert np.abs(qa[:, 4:] - qb[:, 4:]).max() <= 1e-4 * max(1.0, np.abs(qb[:, 4:]).max())
