@@ -545,7 +545,7 @@ def run_ours(a):
     e2e_value = world * n_rays * a.steps / e2e_s
 
     train = train_bench(nr, local, a.train_steps, n=a.train_rays, layout=a.train_layout) if a.train_steps > 0 else None
-    train_full = (train_bench(nr, local, max(2, a.train_steps // 2), n=a.train_rays, layout="patch", full=True)
+    train_full = (train_bench(nr, local, a.train_steps, n=a.train_rays, layout="patch", full=True)
                   if a.train_steps > 0 else None)
     occupancy = occupancy_bench(nr, local, a.mlp) if a.train_steps > 0 else None
     serving = (serve_bench(nr, local, a.mlp, duration=a.serve_seconds, max_slots=a.serve_slots)
