@@ -453,8 +453,8 @@ def run_reference(a):
 
 # DRAM bytes (read + write) of the field kernel's launches for one frame of the frame workload,
 # from one ncu capture of the sources whose SHA-256 is given (profiles/field_tc_bf16_frame512.md).
-FIELD_TRAFFIC = {"sha256": "1426894afed072136a61070833752d48401fe2c1fbe22338797650bcd3200d4d",
-                 "bytes_per_frame": 152441088 + 43357696}
+FIELD_TRAFFIC = {"sha256": "e1dabf63c3b3cd144ced912779157969124783379d998cb22f4c4ed88a93f56f",
+                 "bytes_per_frame": 152614144 + 43867904}
 FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 
