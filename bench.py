@@ -421,6 +421,8 @@ def sweep_bench(nr, device, n_oracle_pixels=384):
                 rows.append({"mlp": mlp, "feat": feat, "ms": ms, "rays_per_s": cam.width * cam.height / (ms / 1e3),
                              "psnr_vs_oracle_db": (10 * np.log10(1.0 / mse)) if mse > 0 else float("inf"),
                              "max_abs_vs_oracle": float(np.abs(d).max()),
+                             "abs_err_p50_p99_vs_oracle": [float(np.percentile(np.abs(d), 50)),
+                                                           float(np.percentile(np.abs(d), 99))],
                              "psnr_vs_f32_gpu_db": (10 * np.log10(1.0 / mse_gpu)) if mse_gpu > 0 else float("inf")})
         S.close()
         out[variant] = rows
@@ -456,6 +458,20 @@ def run_reference(a):
 FIELD_TRAFFIC = {"sha256": "e1dabf63c3b3cd144ced912779157969124783379d998cb22f4c4ed88a93f56f",
                  "bytes_per_frame": 152614144 + 43867904}
 FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
+
+
+def mlp_flops_per_sample(subj) -> int:
+    """Algorithmic flops (2 per multiply-add) of both MLPs per live sample, unpadded: the
+    residual MLP (PE of 3 + 6 * bands dims and the 64 hidden units, layer 4 seeing [h3, gamma],
+    3 outputs; the pose enters as a bias) and the canonical MLP (2 L hash features, hidden
+    layers of 64, 4 outputs)."""
+    bands = int(subj.get("res_pe_freqs", 6))
+    g = 3 + 6 * bands
+    w = 64
+    res = g * w + w * w + w * w + (w + g) * w + w * 3 if int(subj.get("res_enabled", 1)) else 0
+    hidden = len(subj["mlp_layers"]) - 1
+    can = 2 * int(subj["hash_levels"]) * w + (hidden - 1) * w * w + w * 4
+    return 2 * (res + can)
 
 
 def field_traffic():
@@ -566,6 +582,9 @@ def run_ours(a):
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
     traffic = field_traffic() if a.mma == "sync" and a.mlp in ("bf16", "f16") else None
+    mlp_flops = mlp_flops_per_sample(s)
+    mlp_tflops = mlp_flops * live / (field_ms / 1000.0) / 1e12
+    mlp_peak = peaks.get("bf16_tflops", 1900.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -589,6 +608,13 @@ def run_ours(a):
                      "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of the four field launches of "
                                       "one frame (ncu, profiles/field_tc_bf16_frame512.md), per frame like "
                                       "'achieved'; null once the kernel sources differ from the profiled ones")},
+        "roofline_mlp": ({"kernel": "the two MLPs of the same fused field kernel", "bound": "tensor",
+                          "achieved": mlp_tflops, "peak": mlp_peak, "unit": "TFLOP/s", "frac": mlp_tflops / mlp_peak,
+                          "flops_per_live_sample": mlp_flops,
+                          "peak_source": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback",
+                          "note": "algorithmic MLP flops over the whole kernel time: the MLPs are not the "
+                                  "limiter of this gather-bound kernel"}
+                         if a.mlp in ("bf16", "f16") else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},
         "train_step": train,
