@@ -411,7 +411,8 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
                                  CUDA-core FMAs.  The first such call allocates a scratch buffer of
                                  one 212-float column per thread of one 512-thread block per SM
                                  (66 MB on 152 SMs); nr_render_static refuses the flag
-                                 (NR_EUNSUPPORTED).  Ignored for the other dtypes. */
+                                 (NR_EUNSUPPORTED).  Ignored for the other dtypes and by the
+                                 server, whose slots render concurrently. */
 
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,

@@ -32,7 +32,7 @@
 
 namespace nr {
 
-constexpr int kBwdThreads = 384;   // ~165 registers a thread (512 threads at 128 measured slower)
+constexpr int kBwdThreads = 384;   // ~160 registers a thread (512 threads at 128 measured slower)
 constexpr int kFwdThreads = 512;   // the forward fits 128, so twice the warps hide its gathers
 
 // Rows of a thread's scratch column (sized for the subject's hidden depth H).
@@ -222,8 +222,9 @@ __global__ void __launch_bounds__(256) train_composite_kernel(TrainDev T) {
 }
 
 // ------------------------------------------------------- warp-aggregated scatter-add
-// The samples of a warp lie in order along one ray, so lanes that add into the same cell
-// (hash level cell, weight-volume cell) are runs of consecutive lanes.  run_sum sums the
+// The samples of a warp lie in order along one ray (or a few, when S is not a multiple of
+// 32), so lanes that add into the same cell (hash level cell, weight-volume cell) are runs of
+// consecutive lanes.  run_sum sums the
 // values of each run into its first lane (a segmented suffix sum over shuffles, stopping
 // once no run is longer than the distance reached) and returns whether this lane heads a
 // valid run: only head lanes issue the atomics, with the run's totals.  A run is a maximal
