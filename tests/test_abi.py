@@ -59,3 +59,24 @@ def test_struct_sizes_match_header(nr):
     # nr_camera: 2 u32 + 4 f + 9 f + 3 f + 2 f + u32 + 3 f = 24 * 4 bytes
     assert C.sizeof(nr.nr_camera) == 96
     assert C.sizeof(nr.nr_render_opts) == 24
+
+
+def _header_constants():
+    """#define NR_X <n> and the enumerators of nr_status / nr_dtype, from include/nr.h."""
+    text = open(os.path.join(ROOT, "include", "nr.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (NR_\w+) (\d+)u?\b", text, flags=re.M)}
+    for body in re.findall(r"typedef enum \{(.*?)\}", text, flags=re.S):
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        for name, val in re.findall(r"(NR_\w+)\s*=\s*(\d+)", body):
+            consts[name] = int(val)
+    return consts
+
+
+def test_binding_constants_match_header(nr):
+    """Every constant the header defines has the same value in the Python binding."""
+    consts = _header_constants()
+    assert {"NR_OK", "NR_EUNSUPPORTED", "NR_BF16", "NR_RENDER_F32_TC", "NR_TRAIN_ALL", "NR_PARAM_CNN"} <= set(consts)
+    missing = [k for k in consts if not hasattr(nr, k)]
+    assert not missing, missing
+    wrong = {k: (v, getattr(nr, k)) for k, v in consts.items() if getattr(nr, k) != v}
+    assert not wrong, wrong
