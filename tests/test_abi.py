@@ -80,3 +80,38 @@ def test_binding_constants_match_header(nr):
     assert not missing, missing
     wrong = {k: (v, getattr(nr, k)) for k, v in consts.items() if getattr(nr, k) != v}
     assert not wrong, wrong
+
+
+STRUCTS = ["nr_subject_desc", "nr_camera", "nr_render_opts", "nr_train_batch", "nr_request", "nr_server_stats"]
+
+
+def test_struct_layouts_match_header(nr, tmp_path):
+    """sizeof and every field offset of the header's structs, as a C compiler lays them out,
+    equal the ctypes structures of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nr.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append(f'  printf("{s} sizeof %zu\\n", sizeof({s}));')
+        for name, _ in getattr(nr, s)._fields_:
+            lines.append(f'  printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            s, f, v = ln.split()
+            got[(s, f)] = int(v)
+    for s in STRUCTS:
+        cls = getattr(nr, s)
+        assert got[(s, "sizeof")] == C.sizeof(cls), (s, got[(s, "sizeof")], C.sizeof(cls))
+        for name, _ in cls._fields_:
+            assert got[(s, name)] == getattr(cls, name).offset, (s, name)
