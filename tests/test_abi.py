@@ -115,3 +115,27 @@ def test_struct_layouts_match_header(nr, tmp_path):
         assert got[(s, "sizeof")] == C.sizeof(cls), (s, got[(s, "sizeof")], C.sizeof(cls))
         for name, _ in cls._fields_:
             assert got[(s, name)] == getattr(cls, name).offset, (s, name)
+
+
+@pytest.mark.parametrize("field,value,message", [
+    ("level_res", "huge", b"level_res must be 1..65536"),
+    ("wvol_res", 300, b"wvol_res must be 2..256"),
+    ("log2_T", 9, b"log2_T must be 10..24"),
+    ("mlp_hidden_layers", 5, b"mlp_hidden_layers must be 1..4"),
+    ("occ_grid", 100, b"occ_grid"),
+])
+def test_descriptor_checks_without_gpu(nr, field, value, message):
+    """A descriptor outside the documented ranges is refused (NR_EINVAL, with the message)
+    before any device call."""
+    from paper_2306_16541_gb300 import synth
+    s = dict(synth.subject(5))
+    if value == "huge":
+        lv = np.array(s["level_res"], np.uint32)
+        lv[-1] = 70000
+        s["level_res"] = lv
+    else:
+        s[field] = value
+    with pytest.raises(nr.NRError) as e:
+        nr.nr_create_subject(s, stream=0)   # the legacy default stream: no torch CUDA call
+    assert e.value.code == nr.NR_EINVAL
+    assert message in nr.lib.nr_last_error()
