@@ -374,28 +374,44 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
                               "mean_service_ms": float(np.mean(service))}}
 
 
-def sweep_bench(nr, device, n_oracle_pixels=384):
+SWEEP_REFERENCE = os.path.join(ROOT, "tests", "golden", "sweep_oracle_pixels.txt")
+
+
+def sweep_reference() -> dict:
+    """The FP64 oracle's RGBA at the sweep's pixels, stored by tests/golden/make_sweep_reference.py:
+    {variant: (px, py, rgba [n][4])}."""
+    rows = {}
+    with open(SWEEP_REFERENCE) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            rows.setdefault(t[0], []).append([float(v) for v in t[1:]])
+    out = {}
+    for name, r in rows.items():
+        a = np.array(r, np.float64)
+        out[name] = (a[:, 0].astype(np.int64), a[:, 1].astype(np.int64), a[:, 2:6])
+    return out
+
+
+def sweep_bench(nr, device):
     """Precision sweep: 1920x1080, 192 samples per ray, the tiny workload's field with 2^20
     entries per level (and a textured variant), no occupancy.  Every MLP tier (f32 on CUDA
     cores, f32_tc = float32 accuracy on the tensor cores, bf16, f16, fp8) x hash-feature tier
-    (f32, f16): rays/s (CUDA events), PSNR and max-abs against the FP64 oracle on sampled
-    pixels, and PSNR against the f32 GPU image."""
+    (f32, f16): rays/s (CUDA events), PSNR, max-abs and per-pixel error percentiles against the
+    FP64 oracle's values at seeded pixels (stored by tests/golden/make_sweep_reference.py), and
+    PSNR against the f32 GPU image."""
     import torch
-    from oracle import field as OF
-    from oracle import render as OR
     from paper_2306_16541_gb300 import synth
-    cfg = synth.config_sweep()
+    cfg, variants = synth.sweep_variants()
     cam = cfg["camera"]
-    cam.n_samples = 192
+    stored = sweep_reference()
+    px, py = synth.sweep_pixels(cam.width, cam.height)
     out = {}
-    for variant, subj in (("as_configured", cfg["subject"]),
-                          ("textured", synth.subject(1237, log2_t=20, hash_scale=0.5, res_last_std=0.02))):
-        subj = dict(subj)
-        subj["hash_table"] = subj["hash_table"].astype(np.float16).astype(np.float32)   # f16-exact entries
-        rng = np.random.default_rng(11)
-        px = rng.integers(0, cam.width, n_oracle_pixels)
-        py = rng.integers(0, cam.height, n_oracle_pixels)
-        ref = OR.render_pixels(subj, OF.Params(subj), cfg["pose"], cam, px, py, False).numpy()
+    for variant, subj in variants:
+        spx, spy, ref = stored[variant]
+        if not (np.array_equal(spx, px) and np.array_equal(spy, py)):
+            raise RuntimeError(f"{SWEEP_REFERENCE} holds other pixels than the sweep's; regenerate it")
         S = nr.Subject(subj, device=device)
         S.set_pose(*cfg["pose"])
         img = torch.empty(cam.height, cam.width, 4, device="cuda")
@@ -427,7 +443,7 @@ def sweep_bench(nr, device, n_oracle_pixels=384):
         S.close()
         out[variant] = rows
     return {"workload": "1920x1080, 192 samples, 8x2 levels of 2^20 entries, MLP 32-64-64-4, no occupancy",
-            "oracle_pixels": n_oracle_pixels, "tiers": out}
+            "oracle_pixels": int(len(px)), "oracle_values": "tests/golden/sweep_oracle_pixels.txt", "tiers": out}
 
 
 def run_reference(a):

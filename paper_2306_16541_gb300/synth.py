@@ -465,6 +465,26 @@ def config_sweep(seed: int = 1237) -> dict:
                 use_occupancy=True)
 
 
+def sweep_variants() -> tuple:
+    """The precision sweep's inputs: the 1920x1080 x 192 workload and its two fields, the
+    workload's own subject and a textured one (2^20 entries per level), both with hash entries
+    rounded to f16 so that the f16 table tier stores them exactly."""
+    cfg = config_sweep()
+    out = []
+    for name, subj in (("as_configured", cfg["subject"]),
+                       ("textured", subject(1237, log2_t=20, hash_scale=0.5, res_last_std=0.02))):
+        subj = dict(subj)
+        subj["hash_table"] = subj["hash_table"].astype(np.float16).astype(np.float32)
+        out.append((name, subj))
+    return cfg, out
+
+
+def sweep_pixels(width: int, height: int, n: int = 384, seed: int = 11) -> tuple:
+    """The seeded pixels at which the precision sweep compares each tier with the oracle."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, width, n), rng.integers(0, height, n)
+
+
 def training_frames(seed: int, n_frames: int = 16, res: int = 512) -> dict:
     """Seeded poses (<= 30 deg per bone) and cameras on the 2.5 m sphere for n frames."""
     r = _rngs(seed)
