@@ -476,6 +476,15 @@ FIELD_TRAFFIC = {"sha256": "e1dabf63c3b3cd144ced912779157969124783379d998cb22f4c
 FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 
+def field_bytes_per_sample(subj, table_bytes: int = 2) -> int:
+    """Algorithmic bytes of the field kernel per live sample: the 8 corners of every bone
+    channel of the float32 weight volume (24 x 8 x 4 B), the 8 corners of every hash level
+    (L x 8 x 2 features x table_bytes), the sample read (x, y, z, delta: 16 B) and its
+    (r, g, b, alpha) written (16 B)."""
+    n_bones = len(subj["parents"])
+    return n_bones * 8 * 4 + int(subj["hash_levels"]) * 8 * int(subj["hash_feats"]) * table_bytes + 16 + 16
+
+
 def mlp_flops_per_sample(subj) -> int:
     """Algorithmic flops (2 per multiply-add) of both MLPs per live sample, unpadded: the
     residual MLP (PE of 3 + 6 * bands dims and the 64 hidden units, layer 4 seeing [h3, gamma],
@@ -587,10 +596,7 @@ def run_ours(a):
     field_ms = statistics.mean(s["field_ms"] for s in stages)
     live = statistics.mean(s["live_samples"] for s in stages)
     s = cfg["subject"]
-    L = int(s["hash_levels"])
-    # algorithmic bytes per live sample: 24 bones x 8 corners x 4 B of the weight volume,
-    # L levels x 8 corners x 2 features x 2 B of f16 table, 16 B sample in, 16 B (rgb, alpha) out
-    bytes_per_sample = 24 * 8 * 4 + L * 8 * 2 * 2 + 16 + 16
+    bytes_per_sample = field_bytes_per_sample(s, table_bytes=2)
     achieved = bytes_per_sample * live / (field_ms / 1000.0) / 1e9
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
