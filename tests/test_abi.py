@@ -139,3 +139,20 @@ def test_descriptor_checks_without_gpu(nr, field, value, message):
         nr.nr_create_subject(s, stream=0)   # the legacy default stream: no torch CUDA call
     assert e.value.code == nr.NR_EINVAL
     assert message in nr.lib.nr_last_error()
+
+
+def test_option_and_camera_marshalling(nr):
+    """make_opts and make_camera fill the C structs field by field (no device needed)."""
+    from paper_2306_16541_gb300 import synth
+    o = nr.make_opts("bf16", "f16", True, 1e-4, profile=True, mma2=True, all_bones=True)
+    assert (o.mlp_dtype, o.feat_dtype, o.use_occupancy) == (nr.NR_BF16, nr.NR_F16, 1)
+    assert abs(o.t_min - 1e-4) < 1e-9
+    assert o.flags == nr.NR_RENDER_PROFILE | nr.NR_RENDER_MMA2 | nr.NR_RENDER_ALL_BONES
+    o = nr.make_opts("f32", f32_tc=True, tcgen05=True)
+    assert o.mlp_dtype == nr.NR_F32 and o.flags == nr.NR_RENDER_F32_TC | nr.NR_RENDER_TCGEN05
+    cam = synth.camera(64, 48, 80.0, (0.0, 0.0, 2.5), 32, 1.5, 3.5)
+    c = nr.make_camera(cam)
+    assert (c.width, c.height, c.n_samples) == (64, 48, 32)
+    assert (c.fx, c.fy) == (80.0, 80.0) and (c.t_near, c.t_far) == (1.5, 3.5)
+    assert np.allclose(np.array(c.R[:]), np.asarray(cam.R, np.float32).ravel())
+    assert np.allclose(np.array(c.t[:]), np.asarray(cam.t, np.float32).ravel())
