@@ -49,8 +49,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mma", choices=["tcgen05", "sync", "sync2"], default="sync",
-                   help="bf16/f16 MLP path: tcgen05.mma with TMEM accumulators, or warp-level mma.sync")
+    p.add_argument("--mma", choices=["pipeline", "tcgen05", "sync", "sync2"], default="pipeline",
+                   help="bf16/f16 MLP path: the warp-specialised tcgen05 pipeline (default), tcgen05 with one "
+                        "group per tile, or warp-level mma.sync over one or two m-tiles")
     p.add_argument("--cpu-pixels", type=int, default=24576)
     p.add_argument("--train-steps", type=int, default=5)
     p.add_argument("--train-only", action="store_true", help="time only the training step")
@@ -536,7 +537,8 @@ def run_ours(a):
     n_rays = W * H
     t5 = a.mma == "tcgen05" and a.mlp in ("bf16", "f16")
     m2 = a.mma == "sync2"
-    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True, tcgen05=t5, mma2=m2)
+    ms = a.mma == "sync"
+    opts = nr.make_opts(a.mlp, "f16", True, 1e-4, profile=True, tcgen05=t5, mma2=m2, mma_sync=ms)
     S = nr.Subject(cfg["subject"], device=local)
     out = torch.empty(H, W, 4, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -572,7 +574,7 @@ def run_ours(a):
     # end to end through the C ABI with host buffers: pose from host memory,
     # image into pinned host memory (the library copies it back), wall clock
     host_out = torch.empty(H, W, 4, dtype=torch.float32).pin_memory()
-    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4, tcgen05=t5, mma2=m2)
+    opts_e2e = nr.make_opts(a.mlp, "f16", True, 1e-4, tcgen05=t5, mma2=m2, mma_sync=ms)
     for i in range(2):
         S.set_pose(*poses[i])
         nr.nr_render(S.h, cam, opts_e2e, host_out)

@@ -207,19 +207,25 @@ nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_render_opts *o
 /* nr_render without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot let the library call
  * cudaMalloc at render time -- a real-time serving thread that must not
- * stall on the implicit device synchronisation of an allocation, a process
- * that has already handed all free device memory to its own pool, or code
- * recording a CUDA stream capture, where allocation is not permitted.
- * It renders exactly like nr_render, but its work queues live in one
- * fixed, file-scope device array of 8.5 MiB per device (every GPU that
- * loads the library holds it until the process exits) instead of buffers
- * the subject allocates.
+ * stall on the implicit device synchronisation of an allocation, or a
+ * process that has already handed all free device memory to its own pool,
+ * where a late allocation would fail.
+ * It renders the same image as nr_render (same kernels, same compositing
+ * order), but its work queues live in one fixed, file-scope device array of
+ * 8.5 MiB per device (every GPU that loads the library holds it until the
+ * process exits) instead of buffers the subject allocates.
  * Limits: width * height <= 65,536 rays and width * height * n_samples
  * <= 262,144 sample slots; larger frames return NR_EINVAL with a message
  * saying which limit was exceeded.  out_rgba must be device memory
  * (NR_EINVAL otherwise); the subject and its pose must already exist.
+ * Flags: NR_RENDER_MMA_SYNC, NR_RENDER_MMA2, NR_RENDER_TCGEN05 and
+ * NR_RENDER_ALL_BONES are honoured; NR_RENDER_F32_TC and NR_RENDER_PROFILE
+ * need buffers or events created on first use and return NR_EUNSUPPORTED;
+ * NR_FP8E4M3 returns NR_EINVAL.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and must come before any stream capture.
+ * (cudaGetSymbolAddress) and must come before any stream capture; the
+ * address is kept for the process, so the device must not be reset
+ * (cudaDeviceReset) afterwards.
  * All calls on a device share the one array and leave the last call's data
  * in it: calls whose GPU work overlaps (other streams or host threads) race
  * and corrupt each other's results, so serialise them. */
@@ -397,14 +403,24 @@ nr_status nr_set_canonical_occupancy(nr_subject *s, const uint32_t *bits, float 
 nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
 
 #define NR_RENDER_PROFILE 1u  /* nr_render_opts.flags: time each stage with CUDA events */
-#define NR_RENDER_TCGEN05 2u  /* nr_render_opts.flags: bf16/f16 MLPs on tcgen05.mma with TMEM
-                                 accumulators (M = 128 tiles) instead of warp-level mma.sync */
+#define NR_RENDER_TCGEN05 2u  /* nr_render_opts.flags: bf16/f16 MLPs on tcgen05.mma with one group of
+                                 four warps per 128-sample tile issuing its own MMAs and the
+                                 activations passed through shared memory (an earlier design, kept for
+                                 comparison) instead of the default pipeline below */
 #define NR_RENDER_MMA2 4u     /* nr_render_opts.flags: warp-level mma.sync over two 16-row tiles per
-                                 weight-fragment read (12 warps/SM instead of 20) */
+                                 weight-fragment read (12 warps/SM) instead of the default pipeline */
 #define NR_RENDER_ALL_BONES 8u /* nr_render_opts.flags: evaluate all 24 bone channels at every sample.
                                  By default a candidate G_i x is skipped when its trilinear cell lies
                                  outside the index box of channel i's vertices above 1e-7 (weights
                                  that small change S by at most 2.4e-6); training never skips. */
+#define NR_RENDER_MMA_SYNC 32u /* nr_render_opts.flags: bf16/f16 MLPs as warp-level mma.sync m16n8k16 over
+                                 one 16-row tile per weight-fragment read (20 warps/SM, activations in
+                                 registers) instead of the default pipeline.
+                                 The default for NR_BF16 / NR_F16 is the warp-specialised tcgen05
+                                 pipeline: per SM four 128-sample tiles in flight, both MLPs as M = 128
+                                 MMAs with the activations in tensor memory, one issuing warp per tile.
+                                 Its waits are bounded; a wait that gives up makes the call return
+                                 NR_ETIMEOUT (the same holds for NR_RENDER_TCGEN05). */
 #define NR_RENDER_F32_TC 16u  /* nr_render_opts.flags with mlp_dtype NR_F32 (nr_render, nr_query):
                                  both MLPs as warp-level tensor-core layers at float32 accuracy
                                  (each product as three TF32 products of hi/lo parts) instead of
@@ -425,6 +441,14 @@ nr_status nr_stage_times(nr_subject *s, float *ms_out);
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all subjects, all threads). */
 uint64_t nr_launch_count(void);
+
+/* Device address of the subject's field error word (one uint32, allocated with
+ * the subject): the tcgen05 kernels (the bf16/f16 default, NR_RENDER_TCGEN05) set
+ * it when one of their bounded waits gives up; the render or query that launched
+ * them reads it back, returns NR_ETIMEOUT when it is non-zero and clears it.
+ * Instrumentation for tests and monitoring; writing it makes the next such call
+ * report a timeout. */
+nr_status nr_field_error_word(nr_subject *s, uint32_t **dev_word);
 
 /* Thread-local description of the last error ("" if none). */
 const char *nr_last_error(void);

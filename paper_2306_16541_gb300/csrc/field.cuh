@@ -298,10 +298,12 @@ __device__ __forceinline__ void store_relu(const float (&y)[N], float *__restric
   for (int j = 0; j < N; ++j) col[j * stride] = fmaxf(y[j], 0.f);
 }
 
-// 1 / (1 + e^-o) with the fast reciprocal: for o below about -88 the denominator is infinite
-// and an IEEE division would leave its fast path (the result is 0 either way).
-__device__ __forceinline__ float sigmoidf_(float o) { return __fdividef(1.f, 1.f + __expf(-o)); }
-__device__ __forceinline__ float softplusf_(float o) { return fmaxf(o, 0.f) + log1pf(__expf(-fabsf(o))); }
+// The output activations with the accurate expf / log1pf and an IEEE division: rgb =
+// 1 / (1 + e^-o) (0 once e^-o overflows), sigma = max(o, 0) + log(1 + e^-|o|), which never
+// overflows.  The opacity of a sample is formed as -expm1(-sigma delta) so that small
+// sigma delta keep their significant bits.
+__device__ __forceinline__ float sigmoidf_(float o) { return 1.f / (1.f + expf(-o)); }
+__device__ __forceinline__ float softplusf_(float o) { return fmaxf(o, 0.f) + log1pf(expf(-fabsf(o))); }
 
 // Residual MLP (Sec. 4.3, Fig. S3) in float32.  gcol holds gamma(x_skel)
 // (kResGammaPad rows), hcol is the 64-row scratch column; returns x_res.

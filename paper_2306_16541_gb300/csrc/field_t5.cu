@@ -25,6 +25,7 @@
 #include "field.cuh"
 #include "mma.cuh"
 #include "render.cuh"
+#include "t5.cuh"
 
 namespace nr {
 
@@ -33,57 +34,11 @@ constexpr int kT5Threads = 128 * kT5Groups;
 constexpr int kT5TmemCols = 64 * kT5Groups;
 constexpr uint32_t kT5MaxPolls = 1u << 24;
 
-// Byte offsets of the swizzled weight blob (1024-byte aligned matrices of 128-byte rows).
-struct T5Layout {
-  int r1, r2, r3, r4h, r4g, r5, c0, ch[kMaxHidden], cl, total;
-};
-
-__host__ __device__ inline T5Layout t5_layout(int hidden) {
-  T5Layout t{};
-  int o = 0;
-  t.r1 = o; o += 64 * 128;
-  t.r2 = o; o += 64 * 128;
-  t.r3 = o; o += 64 * 128;
-  t.r4h = o; o += 64 * 128;
-  t.r4g = o; o += 64 * 128;
-  t.r5 = o; o += 16 * 128;
-  t.c0 = o; o += 64 * 128;
-  for (int l = 0; l < hidden - 1; ++l) { t.ch[l] = o; o += 64 * 128; }
-  t.cl = o; o += 16 * 128;
-  t.total = o;
-  return t;
-}
-
-// Byte offset of element (row r, column k) of a 64-column 16-bit K-major tile, 128-byte swizzle.
-__host__ __device__ inline int sw128(int r, int k) { return r * 128 + (((k >> 3) ^ (r & 7)) << 4) + ((k & 7) << 1); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: 128-byte swizzle, K-major, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: f32 accumulate, A/B bf16 (fmt 1) or f16 (fmt 0), K-major, M = 128.
-__host__ __device__ inline uint32_t t5_idesc(int n, int fmt) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(128 >> 4) << 24);
-}
-
 __device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void t5_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 
 // Bounded wait for the completion of phase `parity`; false once the poll budget is spent.
@@ -131,30 +86,6 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <typename T>
-struct TcFmt;
-template <>
-struct TcFmt<__nv_bfloat16> {
-  static constexpr int value = 1;
-};
-template <>
-struct TcFmt<__half> {
-  static constexpr int value = 0;
-};
-
-template <typename T>
-__device__ __forceinline__ uint32_t pack2(float a, float b);
-template <>
-__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t *>(&v);
-}
-template <>
-__device__ __forceinline__ uint32_t pack2<__half>(float a, float b) {
-  __half2 v = __floats2half2_rn(a, b);
-  return *reinterpret_cast<uint32_t *>(&v);
 }
 
 // Writes 8-column chunk j (values v[0..7]) of row r of a swizzled tile.
@@ -375,7 +306,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) field_t5_kernel(FieldParams P, 
       const float cr = sigmoidf_(o[0] + sBias[bl.cl]), cg = sigmoidf_(o[1] + sBias[bl.cl + 1]);
       const float cb = sigmoidf_(o[2] + sBias[bl.cl + 2]), sigma = softplusf_(o[3] + sBias[bl.cl + 3]);
       if (MODE == kModeRender) {
-        const float al = inside ? (1.f - __expf(-sigma * delta)) * fminf(S, 1.f) : 0.f;
+        const float al = inside ? -expm1f(-sigma * delta) * fminf(S, 1.f) : 0.f;
         reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, al);
       } else {
         float *q = out + (size_t)NR_QUERY_STRIDE * j;
@@ -429,11 +360,9 @@ static int pack_t5_all(const nr_subject *s, const MasterOffsets &m, cudaStream_t
 nr_status prepare_t5(nr_subject *s, cudaStream_t st) {
   if (s->t5_ready) return NR_OK;
   const T5Layout L = t5_layout((int)s->hidden);
-  if (!s->t5_bf16) {
-    NR_CHECK_CUDA(cudaMalloc(&s->t5_bf16, (size_t)L.total));
-    NR_CHECK_CUDA(cudaMalloc(&s->t5_f16, (size_t)L.total));
-    NR_CHECK_CUDA(cudaMalloc(&s->t5_err, sizeof(uint32_t)));
-    NR_CHECK_CUDA(cudaMemsetAsync(s->t5_err, 0, sizeof(uint32_t), st));
+  if (!s->t5_bf16 || !s->t5_f16) {   // allocated with the subject
+    set_error("tcgen05 weight blobs missing");
+    return NR_ESTATE;
   }
   NR_CHECK_CUDA(cudaMemsetAsync(s->t5_bf16, 0, (size_t)L.total, st));
   NR_CHECK_CUDA(cudaMemsetAsync(s->t5_f16, 0, (size_t)L.total, st));

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(TcCfg<MT>::threads, 1) field_tc_kernel(FieldPa
       const float cr = sigmoidf_(o4[lane * 4 + 0]), cg = sigmoidf_(o4[lane * 4 + 1]);
       const float cb = sigmoidf_(o4[lane * 4 + 2]), sigma = softplusf_(o4[lane * 4 + 3]);
       if (MODE == kModeRender) {
-        const float al = inside ? (1.f - __expf(-sigma * delta)) * fminf(S, 1.f) : 0.f;
+        const float al = inside ? -expm1f(-sigma * delta) * fminf(S, 1.f) : 0.f;
         reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, al);
       } else {
         float *q = out + (size_t)NR_QUERY_STRIDE * j;

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kTf32Threads, 1) field_tf32_kernel(FieldParams
                   o3 = col[(kRowOut + 3) * stride];
       const float cr = sigmoidf_(o0), cg = sigmoidf_(o1), cb = sigmoidf_(o2), sigma = softplusf_(o3);
       if (MODE == kModeRender) {
-        const float a = inside ? (1.f - __expf(-sigma * delta)) * fminf(S, 1.f) : 0.f;
+        const float a = inside ? -expm1f(-sigma * delta) * fminf(S, 1.f) : 0.f;
         reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, a);
       } else {
         float *q = out + (size_t)NR_QUERY_STRIDE * j;

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) field_f32_kernel(FieldParams P
     const float cr = sigmoidf_(o[0]), cg = sigmoidf_(o[1]), cb = sigmoidf_(o[2]);
     const float sigma = softplusf_(o[3]);
     if (MODE == kModeRender) {
-      const float a = inside ? (1.f - __expf(-sigma * delta)) * fminf(S, 1.f) : 0.f;
+      const float a = inside ? -expm1f(-sigma * delta) * fminf(S, 1.f) : 0.f;
       reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, a);
     } else {
       float *q = out + (size_t)NR_QUERY_STRIDE * j;
@@ -391,10 +391,12 @@ int num_sms(int device) {
 
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path) {
-  if ((mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) && mma_path == 1)
-    return launch_field_t5(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
-  if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16)
-    return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st, mma_path == 2 ? 2 : 1);
+  if (mlp_dtype == NR_BF16 || mlp_dtype == NR_F16) {
+    if (mma_path == 1) return launch_field_t5(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
+    if (mma_path == 2 || mma_path == 4)
+      return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st, mma_path == 2 ? 2 : 1);
+    return launch_field_ws(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
+  }
   if (mlp_dtype == NR_FP8E4M3) return launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st);
   if (mlp_dtype != NR_F32) {
     set_error("mlp_dtype %d is not implemented", (int)mlp_dtype);
@@ -416,11 +418,34 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
   return NR_OK;
 }
 
-// The field kernel a render or query takes: 1 tcgen05, 2 two m-tiles per weight read, 3 the
-// float32 tier on the tensor cores, 0 the default of the MLP dtype.
-static int render_path(const nr_render_opts *o) {
+// The field kernel a render or query takes (launch_field's mma_path): for bf16/f16 MLPs 0 the
+// warp-specialised tcgen05 pipeline (the default), 1 tcgen05 with one group per tile and the
+// activations through shared memory, 2 warp-level mma.sync over two m-tiles per weight read,
+// 4 warp-level mma.sync over one m-tile; for float32 3 the tensor-core tier, else CUDA cores.
+int render_path(const nr_render_opts *o) {
   if (o->mlp_dtype == NR_F32) return (o->flags & NR_RENDER_F32_TC) ? 3 : 0;
-  return (o->flags & NR_RENDER_TCGEN05) ? 1 : ((o->flags & NR_RENDER_MMA2) ? 2 : 0);
+  if (o->mlp_dtype != NR_BF16 && o->mlp_dtype != NR_F16) return 0;
+  if (o->flags & NR_RENDER_TCGEN05) return 1;
+  if (o->flags & NR_RENDER_MMA2) return 2;
+  return (o->flags & NR_RENDER_MMA_SYNC) ? 4 : 0;
+}
+
+// Whether the path runs a tcgen05 kernel: it needs the swizzled weight blobs (prepare_t5) and
+// keeps an error word for bounded waits that gave up.
+bool path_uses_tcgen05(const nr_render_opts *o, int path) {
+  return (o->mlp_dtype == NR_BF16 || o->mlp_dtype == NR_F16) && (path == 0 || path == 1);
+}
+
+nr_status check_field_timeouts(nr_subject *s, cudaStream_t st) {
+  if (!s->t5_err) return NR_OK;
+  uint32_t word = 0;
+  NR_CHECK_CUDA(cudaMemcpyAsync(&word, s->t5_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  NR_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (word == 0) return NR_OK;
+  NR_CHECK_CUDA(cudaMemsetAsync(s->t5_err, 0, sizeof(uint32_t), st));
+  set_error("field kernel: a bounded wait on the tensor-core pipeline gave up (code %u); the output is invalid",
+            word);
+  return NR_ETIMEOUT;
 }
 
 // One column of kTf32Rows floats per thread of one block per SM (allocated on first use).
@@ -579,7 +604,8 @@ nr_status render_rays(const nr_subject *s, const FieldParams &P, const uint32_t 
 
 nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t *bits, const nr_camera *cam,
                        const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st) {
-  return render_rays(s, P, bits, cam, opts, w, dst, st, 0, nullptr);
+  const int path = render_path(opts);   // the float32 tensor-core tier needs a scratch buffer: CUDA cores
+  return render_rays(s, P, bits, cam, opts, w, dst, st, path == 3 ? 0 : path, nullptr);
 }
 
 }  // namespace nr
@@ -610,7 +636,8 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const int path = render_path(opts);
-  if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
+  const bool t5 = path_uses_tcgen05(opts, path);
+  if (t5 && (r = prepare_t5(s, st)) != NR_OK) return r;
   if (path == 3 && (r = grow_tf32_scratch(s)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const uint32_t n_rays = cam->width * cam->height;
@@ -661,10 +688,9 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
     s->prof_used = pr.used;
     s->prof_overflow = pr.overflow;
   }
-  if (!dev_out) {
-    NR_CHECK_CUDA(cudaMemcpyAsync(out_rgba, dst, (size_t)n_rays * 16, cudaMemcpyDeviceToHost, st));
-    NR_CHECK_CUDA(cudaStreamSynchronize(st));
-  }
+  if (!dev_out) NR_CHECK_CUDA(cudaMemcpyAsync(out_rgba, dst, (size_t)n_rays * 16, cudaMemcpyDeviceToHost, st));
+  if (t5) return check_field_timeouts(s, st);
+  if (!dev_out) NR_CHECK_CUDA(cudaStreamSynchronize(st));
   return NR_OK;
 }
 
@@ -716,10 +742,13 @@ extern "C" nr_status nr_query(nr_subject *s, uint32_t n, const float *x_obs, con
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->mlp_dtype == NR_FP8E4M3 && (r = prepare_fp8(s, st)) != NR_OK) return r;
   const int path = render_path(opts);
-  if (path == 1 && (r = prepare_t5(s, st)) != NR_OK) return r;
+  const bool t5 = path_uses_tcgen05(opts, path);
+  if (t5 && (r = prepare_t5(s, st)) != NR_OK) return r;
   if (path == 3 && (r = grow_tf32_scratch(s)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   count_launches(1);
-  return launch_field(P, opts->mlp_dtype, kModeQuery, reinterpret_cast<const float4 *>(x_obs), n, nullptr, out,
-                      s->device, st, path);
+  if ((r = launch_field(P, opts->mlp_dtype, kModeQuery, reinterpret_cast<const float4 *>(x_obs), n, nullptr, out,
+                        s->device, st, path)) != NR_OK)
+    return r;
+  return t5 ? check_field_timeouts(s, st) : NR_OK;
 }

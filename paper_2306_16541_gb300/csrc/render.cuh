@@ -113,16 +113,23 @@ nr_status render_frame(const nr_subject *s, const FieldParams &P, const uint32_t
                        const nr_render_opts *opts, const FrameWork &w, float4 *dst, cudaStream_t st);
 
 CamParams cam_params(const nr_camera *c);
+int render_path(const nr_render_opts *o);                     // the launch_field path the options select
+bool path_uses_tcgen05(const nr_render_opts *o, int path);    // needs prepare_t5, sets the error word
+nr_status check_field_timeouts(nr_subject *s, cudaStream_t st);   // NR_ETIMEOUT if a bounded wait gave up
 int num_sms(int device);
 size_t field_f32_smem(const FieldParams &P);
-// mma_path for the bf16/f16 tiers: 0 = warp-level mma.sync over one 16-row m-tile per weight-fragment
-// read (20 warps/SM), 1 = tcgen05 (TMEM accumulators), 2 = mma.sync over two m-tiles per read (12 warps/SM);
-// for the f32 tier: 3 = TF32 tensor-core layers at float32 accuracy (field_tf32.cu), else CUDA cores.
+// mma_path for the bf16/f16 tiers: 0 = the warp-specialised tcgen05 pipeline (field_ws.cu), 1 = tcgen05
+// with one group per tile and activations through shared memory (field_t5.cu), 2 = warp-level mma.sync
+// over two m-tiles per weight read (12 warps/SM), 4 = warp-level mma.sync over one 16-row m-tile per
+// weight-fragment read (20 warps/SM, field_tc.cu); for the f32 tier: 3 = TF32 tensor-core layers at
+// float32 accuracy (field_tf32.cu), else CUDA cores.  Paths 0 and 1 need prepare_t5 first.
 nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                        const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mma_path = 0);
 nr_status launch_field_fp8(const FieldParams &P, int mode, const float4 *in, uint32_t n_fixed, const uint32_t *n_dev,
                            float *out, int device, cudaStream_t st);
 nr_status launch_field_t5(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
+                          const uint32_t *n_dev, float *out, int device, cudaStream_t st);
+nr_status launch_field_ws(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st);
 nr_status launch_field_tc(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st, int mt);

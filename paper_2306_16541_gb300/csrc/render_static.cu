@@ -5,11 +5,12 @@
 // Why: nr_render grows the subject's sample queues with cudaMalloc the first
 // time a frame of a new size arrives.  Some callers cannot allow that at render
 // time: a real-time serving thread where cudaMalloc's implicit device
-// synchronisation would stall every other stream, a process that has handed
-// all free device memory to its own pool, or code running under a stream
-// capture, where allocation calls are not permitted.  This entry point
-// allocates nothing: its scratch is the static array below, created when the
-// module loads, and held by every GPU that loads the library until exit.
+// synchronisation would stall every other stream, or a process that has handed
+// all free device memory to its own pool, so that a late allocation fails.
+// This entry point allocates nothing: its scratch is the static array below,
+// created when the module loads, and held by every GPU that loads the library
+// until exit.  Everything else it touches (parameters, their derived copies,
+// the pose buffers and the occupancy bitfield) was allocated with the subject.
 //
 // Limits: n_rays = width * height <= kStaticRays (65,536) and
 // n_rays * n_samples <= kStaticSamples (262,144 sample slots).  Scratch size:
@@ -23,8 +24,16 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current (the host-side name of
-// a __device__ variable is not a device address).  That look-up may not run
-// under a stream capture: make the first call on each device before capturing.
+// a __device__ variable is not a device address) and keeps it for the process.
+// That look-up may not run under a stream capture: make the first call on each
+// device before any capture.  The kept address belongs to the device's primary
+// context: do not reset the device (cudaDeviceReset) after the first call.
+//
+// Kernel paths: the default path of the MLP dtype (for bf16/f16 the tcgen05
+// pipeline, whose weight blobs and error word come with the subject),
+// NR_RENDER_MMA_SYNC, NR_RENDER_MMA2 and NR_RENDER_TCGEN05 are honoured; NR_RENDER_F32_TC (a scratch buffer
+// allocated on first use) and NR_RENDER_PROFILE (events created on first use)
+// are refused with NR_EUNSUPPORTED.
 #include <mutex>
 
 #include "render.cuh"
@@ -75,6 +84,10 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
     set_error("nr_render_static: NR_RENDER_F32_TC needs a scratch buffer the static path does not allocate");
     return NR_EUNSUPPORTED;
   }
+  if (opts->flags & NR_RENDER_PROFILE) {
+    set_error("nr_render_static: NR_RENDER_PROFILE needs events the static path does not create");
+    return NR_EUNSUPPORTED;
+  }
   NR_REQUIRE(opts->t_min >= 0.f && opts->t_min < 1.f, "nr_render_static: t_min must be in [0, 1)");
   NR_REQUIRE(!opts->use_occupancy || s->occ_source != kOccNone, "nr_render_static: the subject has no occupancy");
   NR_REQUIRE(cam->width >= 1 && cam->height >= 1 && cam->n_samples >= 1 && cam->n_samples <= 1024,
@@ -103,6 +116,9 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
   if ((r = ensure_pose(s, st)) != NR_OK) return r;
   if ((r = ensure_bias(s, st)) != NR_OK) return r;
   if (opts->use_occupancy && (r = ensure_occupancy(s, st)) != NR_OK) return r;
+  const int path = render_path(opts);
+  const bool t5 = path_uses_tcgen05(opts, path);
+  if (t5 && (r = prepare_t5(s, st)) != NR_OK) return r;
   const FieldParams P = field_params(s, opts);
   const CamParams C = cam_params(cam);
   MarchParams mp{};
@@ -119,11 +135,11 @@ extern "C" nr_status nr_render_static(nr_subject *s, const nr_camera *cam, const
   march_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(C, mp, sc->samp, sc->ray_range, sc->counter);
   NR_CHECK_CUDA(cudaGetLastError());
   if ((r = launch_field(P, opts->mlp_dtype, kModeRender, sc->samp, 0, sc->counter, (float *)sc->samp_out, s->device,
-                        st)) != NR_OK)
+                        st, path)) != NR_OK)
     return r;
   composite_kernel<<<(nr_ + 255) / 256, 256, 0, st>>>(sc->ray_range, sc->samp_out, nr_, opts->t_min, cam->bg[0],
                                                       cam->bg[1], cam->bg[2], reinterpret_cast<float4 *>(out_rgba));
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(3);
-  return NR_OK;
+  return t5 ? check_field_timeouts(s, st) : NR_OK;
 }

@@ -52,6 +52,8 @@ struct Slot {
   uint32_t *bits = nullptr;
   FrameWork w{};
   float *h_pose = nullptr;          // pinned: G [24*12], omega [72], root translation [3]
+  uint32_t *d_err = nullptr;        // the field kernels' error word of the request in flight
+  uint32_t *h_err = nullptr;        // pinned copy, read by the completion callback
   size_t bytes = 0;
   bool busy = false;
   uint64_t req = 0;
@@ -107,10 +109,11 @@ static void free_slot(Slot *sl) {
   if (sl->stream) cudaStreamSynchronize(sl->stream);
   if (sl->stream_lo) cudaStreamSynchronize(sl->stream_lo);
   void *bufs[] = {sl->d_G,       sl->d_omega,   sl->d_bias1,      sl->bits,   sl->w.samp,
-                  sl->w.samp_out, sl->w.ray_range, sl->w.counter, sl->w.state, sl->w.next};
+                  sl->w.samp_out, sl->w.ray_range, sl->w.counter, sl->w.state, sl->w.next, sl->d_err};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (sl->h_pose) cudaFreeHost(sl->h_pose);
+  if (sl->h_err) cudaFreeHost(sl->h_err);
   if (sl->stream) cudaStreamDestroy(sl->stream);
   if (sl->stream_lo) cudaStreamDestroy(sl->stream_lo);
   delete sl;
@@ -143,9 +146,12 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
   SLOT_ALLOC(sl->w.counter, 256);
   SLOT_ALLOC(sl->w.state, kSlotRays * sizeof(float4));
   SLOT_ALLOC(sl->w.next, kSlotRays * sizeof(uint32_t));
+  SLOT_ALLOC(sl->d_err, sizeof(uint32_t));
 #undef SLOT_ALLOC
   if ((e = cudaMallocHost((void **)&sl->h_pose, (kBones * 12 + kBones * 3 + 3) * sizeof(float))) != cudaSuccess)
     return fail(e, "pinned pose buffer");
+  if ((e = cudaMallocHost((void **)&sl->h_err, sizeof(uint32_t))) != cudaSuccess) return fail(e, "pinned error word");
+  *sl->h_err = 0;
   sl->w.cap_samples = kSlotSamples;
   sl->w.cap_rays = kSlotRays;
   sl->bytes = slot_bytes(grid);
@@ -164,9 +170,15 @@ static void CUDART_CB on_request_done(void *p) {
   if (it != srv->reqs.end()) {
     Request &q = it->second;
     q.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - q.t_submit).count();
-    q.state = 2;
-    srv->st.completed += 1;
-    srv->st.rays_done += (double)q.r.cam.width * q.r.cam.height;
+    if (*sl->h_err) {   // a bounded wait of a tcgen05 field kernel gave up: the image is invalid
+      q.state = -1;
+      q.err = "field kernel: a bounded wait on the tensor-core pipeline gave up";
+      srv->st.failed += 1;
+    } else {
+      q.state = 2;
+      srv->st.completed += 1;
+      srv->st.rays_done += (double)q.r.cam.width * q.r.cam.height;
+    }
   }
   sl->busy = false;
   srv->st.active -= 1;
@@ -200,11 +212,14 @@ static nr_status launch_request(nr_server *srv, Slot *sl, Request &q, DoneCtx *c
   FieldParams P = field_params(s, &r.opts);
   P.G = sl->d_G;
   P.bias1 = sl->d_bias1;
+  P.t5_err = sl->d_err;             // this slot's own error word: slots render concurrently
+  NR_CHECK_CUDA(cudaMemsetAsync(sl->d_err, 0, sizeof(uint32_t), st));
   // the composite kernel writes the pixels straight into out_rgba (device memory, or
   // pinned host memory reached through the unified address space)
   if ((rc = render_frame(s, P, sl->bits, &r.cam, &r.opts, sl->w, reinterpret_cast<float4 *>(r.out_rgba), st)) !=
       NR_OK)
     return rc;
+  NR_CHECK_CUDA(cudaMemcpyAsync(sl->h_err, sl->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   NR_CHECK_CUDA(cudaLaunchHostFunc(st, on_request_done, ctx));
   return NR_OK;
 }
@@ -315,6 +330,7 @@ extern "C" nr_status nr_server_add_subject(nr_server *srv, nr_subject *s, uint32
   nr_status r;
   if ((r = prepare_params(s, nullptr)) != NR_OK) return r;
   if ((r = prepare_fp8(s, nullptr)) != NR_OK) return r;
+  if ((r = prepare_t5(s, nullptr)) != NR_OK) return r;
   NR_CHECK_CUDA(cudaDeviceSynchronize());
   std::lock_guard<std::mutex> lock(srv->mu);
   NR_REQUIRE(srv->subjects.empty() || srv->subjects[0]->occ_grid == s->occ_grid,

@@ -10,6 +10,7 @@
 
 #include "field.cuh"
 #include "render.cuh"
+#include "t5.cuh"
 
 namespace nr {
 
@@ -655,6 +656,12 @@ extern "C" const char *nr_last_error(void) { return nr::g_err; }
 
 extern "C" uint64_t nr_launch_count(void) { return nr::g_launches.load(std::memory_order_relaxed); }
 
+extern "C" nr_status nr_field_error_word(nr_subject *s, uint32_t **dev_word) {
+  NR_REQUIRE(subject_ok(s) && dev_word, "nr_field_error_word: bad argument");
+  *dev_word = s->t5_err;
+  return NR_OK;
+}
+
 static void free_subject(nr_subject *s) {
   void *bufs[] = {s->wquad,  s->wvol,   s->g_wvol,  s->table,    s->g_table,  s->mlp,       s->g_mlp,     s->res,
                   s->g_res,  s->adam_m,  s->adam_v,   s->table16,  s->dense_quad, s->r_scratch, s->blob,      s->tc_bf16,   s->tc_f16,
@@ -768,6 +775,9 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->bone_ibox, kBones * 6 * sizeof(int));
   ALLOC(s->tc_bf16, (size_t)s->tlay.total * 2);
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
+  ALLOC(s->t5_bf16, (size_t)t5_layout((int)s->hidden).total);   // tcgen05 weight blobs, packed on first use
+  ALLOC(s->t5_f16, (size_t)t5_layout((int)s->hidden).total);
+  ALLOC(s->t5_err, sizeof(uint32_t));
   ALLOC(s->d_G, kBones * 12 * 4);
   ALLOC(s->d_omega, (2 * kBones * 3 + 3) * 4);
   ALLOC(s->d_bias1, kWidth * 4);
@@ -781,6 +791,8 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
 #define H2D(dst, src, bytes)                                                   \
   e = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st);      \
   if (e != cudaSuccess) return fail(e, "cudaMemcpyAsync " #dst);
+  e = cudaMemsetAsync(s->t5_err, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return fail(e, "cudaMemsetAsync t5_err");
   H2D(s->wvol, d->wvol, s->n_wvol * 4);
   H2D(s->table, d->hash_table, s->n_table * 4);
   H2D(s->mlp, d->mlp_params, s->n_mlp * 4);

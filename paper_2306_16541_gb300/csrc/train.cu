@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) train_fwd_kernel(FieldParams P
       if (active) {
         const float o0 = col[D_CL * stride], o1 = col[(D_CL + 1) * stride], o2 = col[(D_CL + 2) * stride],
                     o3 = col[(D_CL + 3) * stride];
-        const float a = inside ? (1.f - expf(-softplusf_(o3) * s.w)) * fminf(S, 1.f) : 0.f;
+        const float a = inside ? -expm1f(-softplusf_(o3) * s.w) * fminf(S, 1.f) : 0.f;
         v = make_float4(sigmoidf_(o0), sigmoidf_(o1), sigmoidf_(o2), a);
       }
       T.out[j] = v;
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       const float e = expf(-sig * s.w);
       const float lk = fminf(S, 1.f);
       const float dsig = g4.w * s.w * e * lk;
-      dS_alpha = S < 1.f ? g4.w * (1.f - e) : 0.f;
+      dS_alpha = S < 1.f ? g4.w * -expm1f(-sig * s.w) : 0.f;
       const float gc[3] = {g4.x, g4.y, g4.z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {

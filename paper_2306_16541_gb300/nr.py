@@ -36,6 +36,7 @@ NR_RENDER_ALL_BONES = 8
 NR_RENDER_TCGEN05 = 2
 NR_RENDER_MMA2 = 4
 NR_RENDER_F32_TC = 16
+NR_RENDER_MMA_SYNC = 32
 NR_ABI_VERSION = 1
 
 _fp = C.POINTER(C.c_float)
@@ -115,6 +116,7 @@ def _load() -> C.CDLL:
         "nr_render_static": ([vp, C.POINTER(nr_camera), C.POINTER(nr_render_opts), vp, vp], C.c_int),
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
+        "nr_field_error_word": ([vp, C.POINTER(vp)], C.c_int),
         "nr_server_create": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(vp)], C.c_int),
         "nr_server_add_subject": ([vp, vp, C.POINTER(C.c_uint32)], C.c_int),
         "nr_server_submit": ([vp, C.POINTER(nr_request), C.POINTER(C.c_uint64)], C.c_int),
@@ -175,13 +177,14 @@ def make_camera(cam) -> nr_camera:
 
 def make_opts(mlp: str = "f32", feat: str = "f32", occupancy: bool = False, t_min: float = 0.0,
               hann_alpha: float = -1.0, profile: bool = False, tcgen05: bool = False,
-              mma2: bool = False, all_bones: bool = False, f32_tc: bool = False) -> nr_render_opts:
+              mma2: bool = False, all_bones: bool = False, f32_tc: bool = False,
+              mma_sync: bool = False) -> nr_render_opts:
     o = nr_render_opts()
     o.mlp_dtype, o.feat_dtype = DTYPES[mlp], DTYPES[feat]
     o.use_occupancy, o.t_min, o.hann_alpha = int(bool(occupancy)), float(t_min), float(hann_alpha)
     o.flags = ((NR_RENDER_PROFILE if profile else 0) | (NR_RENDER_TCGEN05 if tcgen05 else 0)
                | (NR_RENDER_MMA2 if mma2 else 0) | (NR_RENDER_ALL_BONES if all_bones else 0)
-               | (NR_RENDER_F32_TC if f32_tc else 0))
+               | (NR_RENDER_F32_TC if f32_tc else 0) | (NR_RENDER_MMA_SYNC if mma_sync else 0))
     return o
 
 

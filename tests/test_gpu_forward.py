@@ -270,16 +270,16 @@ def test_tcgen05_path_psnr_and_agreement(tiny_structured, frame, mlp):
 def test_two_tile_path_equals_default(frame, mlp):
     """NR_RENDER_MMA2 (two 16-row tiles per weight-fragment read, each layer taken in
     output-column order) issues the same MMAs on every accumulator, in the same order, as
-    the default path: images and query rows are bitwise equal, a ragged tail included."""
+    the one-tile mma.sync path: images and query rows are bitwise equal, a ragged tail included."""
     nr = nrmod()
     cam = _small(frame["camera"], 96)
     x = torch.from_numpy(np.random.default_rng(10).uniform(-0.9, 0.9, size=(1001, 3)).astype(np.float32)).cuda()
     S = nr.Subject(frame["subject"])
     try:
         S.set_pose(*frame["pose"])
-        a = S.render(cam, nr.make_opts(mlp, "f16", True, 1e-4))
+        a = S.render(cam, nr.make_opts(mlp, "f16", True, 1e-4, mma_sync=True))
         b = S.render(cam, nr.make_opts(mlp, "f16", True, 1e-4, mma2=True))
-        qa = S.query(x, nr.make_opts(mlp, "f16"))
+        qa = S.query(x, nr.make_opts(mlp, "f16", mma_sync=True))
         qb = S.query(x, nr.make_opts(mlp, "f16", mma2=True))
         torch.cuda.synchronize()
     finally:
