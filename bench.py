@@ -447,34 +447,54 @@ def sweep_bench(nr, device):
             "oracle_pixels": int(len(px)), "oracle_values": "tests/golden/sweep_oracle_pixels.txt", "tiers": out}
 
 
+def oracle_pixels_time(cfg, poses, n_pixels, seed):
+    """Seconds the FP64 oracle, as it stands, takes for n_pixels random pixels of the frame."""
+    from oracle import field as OF
+    from oracle import render as OR
+    cam = cfg["camera"]
+    rng = np.random.default_rng(seed)
+    px = rng.integers(0, cam.width, n_pixels)
+    py = rng.integers(0, cam.height, n_pixels)
+    P = OF.Params(cfg["subject"])
+    t0 = time.perf_counter()
+    OR.render_pixels(cfg["subject"], P, poses[0], cam, px, py, True)
+    return time.perf_counter() - t0
+
+
 def run_reference(a):
+    """The reference arm: the FP64 oracle on the host cores; a step is 256 random pixels of the
+    512 x 512 x 128 frame (the whole frame would take minutes), timed as it runs."""
+    import torch
     rank, world, local = dist_setup(a.gpus)
     if rank != 0:
         return
     cfg, poses = workload()
-    vals = []
+    n_px = 256
+    times = []
     for i in range(a.warmup + a.steps):
-        r = cpu_baseline(cfg, poses, 256, seed=i)
+        dt = oracle_pixels_time(cfg, poses, n_px, seed=i)
         if i >= a.warmup:
-            vals.append(r["value"])
-    ms_per_step = 1000.0 * 512 * 512 / statistics.mean(vals)
-    v = statistics.mean(vals)
-    base = cpu_baseline(cfg, poses, 256, seed=99)
+            times.append(dt)
+    step_s = statistics.mean(times)
+    v = n_px / step_s
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "frame_512x512_s128_occupancy", "sample_per_step": "256 random pixels"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
-                             "sample": "256 random pixels of one 512x512 frame per step, FP64 torch CPU"},
+            "config": {"workload": "frame_512x512_s128_occupancy",
+                       "sample_per_step": f"{n_px} random pixels of one 512x512 frame (128 samples each)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{n_px} random pixels of one 512x512 frame per step, FP64 torch CPU, "
+                                       f"mean of {a.steps} steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-# DRAM bytes (read + write) of the field kernel's launches for one frame of the frame workload,
-# from one ncu capture of the sources whose SHA-256 is given (profiles/field_tc_bf16_frame512.md).
-FIELD_TRAFFIC = {"sha256": "e1dabf63c3b3cd144ced912779157969124783379d998cb22f4c4ed88a93f56f",
-                 "bytes_per_frame": 152614144 + 43867904}
-FIELD_SOURCES = ["field_tc.cu", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
+# Per frame of the frame workload, from one ncu capture of the four field launches of a frame on
+# the default bf16 path, valid while the kernel sources have the SHA-256 given: DRAM bytes read +
+# written, and the bytes of the L1 sectors the global loads touched.
+FIELD_CAPTURE = {"sha256": None, "dram_bytes_per_frame": None, "l1_sector_bytes_per_frame": None,
+                 "live_samples_per_frame": None}
+FIELD_SOURCES = ["field_ws.cu", "gather.cuh", "t5.cuh", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 
 def field_bytes_per_sample(subj, table_bytes: int = 2) -> int:
@@ -489,24 +509,46 @@ def field_bytes_per_sample(subj, table_bytes: int = 2) -> int:
 def mlp_flops_per_sample(subj) -> int:
     """Algorithmic flops (2 per multiply-add) of both MLPs per live sample, unpadded: the
     residual MLP (PE of 3 + 6 * bands dims and the 64 hidden units, layer 4 seeing [h3, gamma],
-    3 outputs; the pose enters as a bias) and the canonical MLP (2 L hash features, hidden
+    3 outputs; the pose enters as a bias) and the canonical MLP (L x F hash features, hidden
     layers of 64, 4 outputs)."""
     bands = int(subj.get("res_pe_freqs", 6))
     g = 3 + 6 * bands
     w = 64
     res = g * w + w * w + w * w + (w + g) * w + w * 3 if int(subj.get("res_enabled", 1)) else 0
     hidden = len(subj["mlp_layers"]) - 1
-    can = 2 * int(subj["hash_levels"]) * w + (hidden - 1) * w * w + w * 4
+    can = int(subj["hash_levels"]) * int(subj["hash_feats"]) * w + (hidden - 1) * w * w + w * 4
     return 2 * (res + can)
 
 
-def field_traffic():
+def field_capture():
+    """The ncu figures of FIELD_CAPTURE if the kernel sources are still the captured ones, else None."""
     import hashlib
+    if FIELD_CAPTURE["sha256"] is None:
+        return None
     h = hashlib.sha256()
     for f in FIELD_SOURCES:
         with open(os.path.join(ROOT, "paper_2306_16541_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return float(FIELD_TRAFFIC["bytes_per_frame"]) if h.hexdigest() == FIELD_TRAFFIC["sha256"] else None
+    return FIELD_CAPTURE if h.hexdigest() == FIELD_CAPTURE["sha256"] else None
+
+
+def gather_ceiling(nr, device, subj, hbm_gbs):
+    """The measured ceiling of the field kernel's algorithmic bytes: L2-resident random gathers of
+    4 B (hashed levels) and 16 B (corner blocks of the weight volume and of the dense levels),
+    measured now on this GPU (nr_l2_gather_rate, a table of the f16 hash table's size), mixed by the
+    kernel's byte counts per live sample; the sample's own 32 B stream from HBM."""
+    table = 1 << (int(subj["log2_T"]) + 2 + 4)            # 2^log2_T entries x 4 B x 16 levels
+    r4 = nr.nr_l2_gather_rate(device, table, 4) / 1e9
+    r16 = nr.nr_l2_gather_rate(device, table, 16) / 1e9
+    levels = [int(v) for v in subj["level_res"]]
+    T = 1 << int(subj["log2_T"])
+    dense = sum(1 for n in levels if (n + 1) ** 3 <= T)
+    feat_b = int(subj["hash_feats"]) * 2
+    b16 = len(subj["parents"]) * 8 * 4 + dense * 8 * feat_b
+    b4 = (len(levels) - dense) * 8 * feat_b
+    t = b16 / r16 + b4 / r4 + 32 / hbm_gbs               # ns per live sample at the ceilings
+    return {"gbs": (b16 + b4 + 32) / t, "gather_4B_gbs": r4, "gather_16B_gbs": r16,
+            "bytes_16B": b16, "bytes_4B": b4, "bytes_stream": 32}
 
 
 def run_ours(a):
@@ -605,10 +647,28 @@ def run_ours(a):
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
-    traffic = field_traffic() if a.mma == "sync" and a.mlp in ("bf16", "f16") else None
+    ceiling = gather_ceiling(nr, local, s, hbm)
+    default_path = a.mma == "pipeline" and a.mlp in ("bf16", "f16")
+    cap = field_capture() if default_path else None
+    # bytes the kernel requests: the bone channels it reads (counted by the profiled renders), the
+    # hash corners and the sample's own stream; and the gather ceiling of that mix
+    bones_read = statistics.mean(s_["bones_read_per_sample"] for s_ in stages)
+    requested = None
+    if bones_read > 0:
+        b16_req = bones_read * 8 * 4 + ceiling["bytes_16B"] - len(s["parents"]) * 8 * 4
+        t_req = b16_req / ceiling["gather_16B_gbs"] + ceiling["bytes_4B"] / ceiling["gather_4B_gbs"] + 32 / hbm
+        req_bytes = b16_req + ceiling["bytes_4B"] + 32
+        req_ach = req_bytes * live / (field_ms / 1000.0) / 1e9
+        requested = {"bytes_per_live_sample": req_bytes, "bone_channels_read": bones_read,
+                     "achieved": req_ach, "peak": req_bytes / t_req, "frac": req_ach / (req_bytes / t_req)}
     mlp_flops = mlp_flops_per_sample(s)
     mlp_tflops = mlp_flops * live / (field_ms / 1000.0) / 1e12
     mlp_peak = peaks.get("bf16_tflops", 1900.0)
+    mlp_peak_sus = peaks.get("bf16_tflops_sustained", 1700.0)
+    kernel_name = {"pipeline": "field_ws_kernel (warp-specialised tcgen05)", "tcgen05": "field_t5_kernel",
+                   "sync": "field_tc_kernel (mma.sync)", "sync2": "field_tc_kernel (mma.sync, two m-tiles)"}[a.mma]
+    if a.mlp == "f32":
+        kernel_name = "field_f32_kernel"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -616,28 +676,48 @@ def run_ours(a):
         "config": {"workload": "frame_512x512_s128_occupancy", "image": [W, H], "samples_per_ray": 128,
                    "occupancy_grid": 128, "hash": "16x2 levels, 2^19 f16 entries, N 16..2048",
                    "mlp": f"32-64-64-64-4 {a.mlp}", "residual_mlp": f"6 PE bands, width 64, {a.mlp}",
-                   "mma_path": ("tcgen05 (TMEM accumulators, M=128 tiles)" if t5 else
-                                ("mma.sync m16n8k16" if a.mlp in ("bf16", "f16") else "CUDA cores")),
+                   "mma_path": kernel_name,
                    "weight_volume": "64^3 x 25 f32", "ert_t_min": 1e-4, "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MiB write) between timed steps"},
         "samples_per_s": world * live * a.steps / (total_ms / 1000.0),
         "live_samples_per_frame": live,
         "stage_ms": {k: statistics.mean(st[k] for st in stages) for k in ("march_ms", "field_ms", "composite_ms")},
-        "roofline": {"kernel": ("field_t5_kernel" if t5 else "field kernel") +
-                               " (fused LBS warp + residual MLP + hash + canonical MLP)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                     "bytes_per_live_sample": bytes_per_sample,
-                     "traffic": traffic,
+        "roofline": {"kernel": kernel_name + ": fused LBS warp + residual MLP + hash + canonical MLP",
+                     "bound": "l2",
+                     "achieved": requested["achieved"] if requested else achieved,
+                     "peak": requested["peak"] if requested else ceiling["gbs"], "unit": "GB/s",
+                     "frac": requested["frac"] if requested else achieved / ceiling["gbs"],
+                     "basis": ("requested bytes: the bone channels the kernel reads (measured per frame), "
+                               "the hash corners and the sample stream" if requested else "counted bytes"),
+                     "peak_source": ("measured in this run: L2-resident random gathers (nr_l2_gather_rate) of "
+                                     f"4 B at {ceiling['gather_4B_gbs']:.0f} GB/s and 16 B at "
+                                     f"{ceiling['gather_16B_gbs']:.0f} GB/s, weighted by the kernel's "
+                                     f"{ceiling['bytes_4B']} B of 4-byte and {ceiling['bytes_16B']} B of 16-byte "
+                                     "gathers per live sample, its 32 B sample stream at the measured HBM rate"),
+                     "counted": {"bytes_per_live_sample": bytes_per_sample, "achieved": achieved,
+                                 "peak": ceiling["gbs"], "frac": achieved / ceiling["gbs"]},
+                     "requested": requested,
+                     "bytes_per_live_sample": {
+                         "counted": bytes_per_sample,
+                         "l1_sector_bytes": (cap["l1_sector_bytes_per_frame"] / cap["live_samples_per_frame"]
+                                             if cap else None),
+                         "note": "counted: all 24 bone channels (768 B) + 16 hash levels (512 B) + sample in/out; "
+                                 "the kernel skips bone channels whose support misses the candidate and reads "
+                                 "L1 sectors of 32 B, so it moves a different number of bytes through L1"},
+                     "vs_hbm": {"frac": achieved / hbm, "peak": hbm,
+                                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+                     "traffic": cap["dram_bytes_per_frame"] if cap else None,
                      "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of the four field launches of "
-                                      "one frame (ncu, profiles/field_tc_bf16_frame512.md), per frame like "
-                                      "'achieved'; null once the kernel sources differ from the profiled ones")},
+                                      "one frame from the ncu capture of these kernel sources, per frame like "
+                                      "'achieved'; null on another path or once the sources differ")},
         "roofline_mlp": ({"kernel": "the two MLPs of the same fused field kernel", "bound": "tensor",
-                          "achieved": mlp_tflops, "peak": mlp_peak, "unit": "TFLOP/s", "frac": mlp_tflops / mlp_peak,
-                          "flops_per_live_sample": mlp_flops,
-                          "peak_source": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback",
-                          "note": "algorithmic MLP flops over the whole kernel time: the MLPs are not the "
-                                  "limiter of this gather-bound kernel"}
+                          "achieved": mlp_tflops, "unit": "TFLOP/s", "flops_per_live_sample": mlp_flops,
+                          "peak": mlp_peak, "frac": mlp_tflops / mlp_peak,
+                          "peak_sustained": mlp_peak_sus, "frac_sustained": mlp_tflops / mlp_peak_sus,
+                          "peak_source": ("measured bf16 burst / sustained" if "bf16_tflops" in peaks
+                                          else "fallback"),
+                          "note": "algorithmic MLP flops over the whole field-kernel time: the gathers, not "
+                                  "the tensor cores, bound this kernel"}
                          if a.mlp in ("bf16", "f16") else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},

@@ -433,8 +433,11 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
 /* Stage times in milliseconds of the subject's last nr_render call made with
  * NR_RENDER_PROFILE: ms_out[0] ray marching, [1] the per-sample field,
  * [2] compositing (each summed over ray chunks), [3] the number of field
- * launches (ray chunks), [4] the number of live samples the field evaluated.
- * ms_out holds 5 floats.  CUDA events on the render's stream bracket every launch; this
+ * launches (ray chunks), [4] the number of live samples the field evaluated,
+ * [5] the mean number of weight-volume bone channels the field read per live
+ * sample (channels whose support holds the candidate; the default bf16/f16
+ * pipeline counts them, other paths report 0).
+ * ms_out holds 6 floats.  CUDA events on the render's stream bracket every launch; this
  * call waits for them.  NR_ESTATE if no profiled render has run. */
 nr_status nr_stage_times(nr_subject *s, float *ms_out);
 
@@ -449,6 +452,15 @@ uint64_t nr_launch_count(void);
  * Instrumentation for tests and monitoring; writing it makes the next such call
  * report a timeout. */
 nr_status nr_field_error_word(nr_subject *s, uint32_t **dev_word);
+
+/* Measured ceiling of the field kernel's gathers (instrumentation; the paper has
+ * no counterpart): the rate, in bytes requested by the threads per second, at
+ * which `device` serves independent random loads of load_bytes (4 or 16,
+ * aligned) from a table of table_bytes (a power of two, 1 MiB .. 1 GiB) that
+ * stays resident in L2 -- the access pattern of the hash-table corners (4 B)
+ * and of the corner blocks (16 B).  Best of three timed launches (CUDA events)
+ * after a warm-up launch; allocates and frees the table. */
+nr_status nr_l2_gather_rate(int device, uint64_t table_bytes, uint32_t load_bytes, double *bytes_per_s);
 
 /* Thread-local description of the last error ("" if none). */
 const char *nr_last_error(void);

@@ -106,6 +106,7 @@ struct FieldParams {
   float occ_smin;                    // least bone-weight sum S of a posed cell
   const uint32_t *canon_bits;        // canonical bitfield read by kModePose
   float *tf32_scratch;               // activation columns of the float32 tensor-core tier (or NULL)
+  uint32_t *kept_count;              // profiled renders: bone channels read, summed over samples (or NULL)
 };
 
 struct Frame {                       // a training frame's camera (decoded)

@@ -387,6 +387,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       const float delta = d_next;
       float s0, s1, s2, S;
       lbs_end(P, sG, nx, s0, s1, s2, S);
+      if (P.kept_count) {   // profiled renders: the bone channels this warp's samples read
+        uint32_t c = valid ? (uint32_t)__popc(nx.mine) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((tid & 31) == 0) atomicAdd(P.kept_count, c);
+      }
       const bool more = tile + tstride < n_tiles;
       if (more) load_in(tile + tstride, nx, d_next);
       int stage = 0;

@@ -639,7 +639,9 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
   const bool t5 = path_uses_tcgen05(opts, path);
   if (t5 && (r = prepare_t5(s, st)) != NR_OK) return r;
   if (path == 3 && (r = grow_tf32_scratch(s)) != NR_OK) return r;
-  const FieldParams P = field_params(s, opts);
+  FieldParams P = field_params(s, opts);
+  const bool prof = (opts->flags & NR_RENDER_PROFILE) != 0;
+  if (prof) P.kept_count = s->counter + 9;
   const uint32_t n_rays = cam->width * cam->height;
   // chunk the rays so that the worst-case sample queue of a round stays below 2^26 entries
   const uint64_t max_samples = 1ull << 26;
@@ -660,7 +662,6 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
     }
     dst = s->out_stage;
   }
-  const bool prof = (opts->flags & NR_RENDER_PROFILE) != 0;
   Prof pr{};
   if (prof) {
     for (int i = 0; i < nr_subject::kProfEvents; ++i)
@@ -710,13 +711,14 @@ extern "C" nr_status nr_stage_times(nr_subject *s, float *ms) {
     acc[s->prof_stage[i]] += t;
     field_launches += s->prof_stage[i] == 1;
   }
-  uint32_t live = 0;
-  NR_CHECK_CUDA(cudaMemcpy(&live, s->counter + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  uint32_t cnt[2] = {0, 0};   // live samples, bone channels read
+  NR_CHECK_CUDA(cudaMemcpy(cnt, s->counter + 8, sizeof(cnt), cudaMemcpyDeviceToHost));
   ms[0] = acc[0];
   ms[1] = acc[1];
   ms[2] = acc[2];
   ms[3] = (float)field_launches;
-  ms[4] = (float)live;
+  ms[4] = (float)cnt[0];
+  ms[5] = cnt[0] ? (float)((double)cnt[1] / (double)cnt[0]) : 0.f;
   if (s->prof_overflow) {
     set_error("nr_stage_times: more launches than profiling events; times are partial");
     return NR_EBUSY;

@@ -117,6 +117,7 @@ def _load() -> C.CDLL:
         "nr_stage_times": ([vp, _fp], C.c_int),
         "nr_launch_count": ([], C.c_uint64),
         "nr_field_error_word": ([vp, C.POINTER(vp)], C.c_int),
+        "nr_l2_gather_rate": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)], C.c_int),
         "nr_server_create": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(vp)], C.c_int),
         "nr_server_add_subject": ([vp, vp, C.POINTER(C.c_uint32)], C.c_int),
         "nr_server_submit": ([vp, C.POINTER(nr_request), C.POINTER(C.c_uint64)], C.c_int),
@@ -190,14 +191,21 @@ def make_opts(mlp: str = "f32", feat: str = "f32", occupancy: bool = False, t_mi
 
 def nr_stage_times(h) -> dict:
     """Stage times (ms) and live-sample count of the last profiled nr_render."""
-    ms = np.zeros(5, np.float32)
+    ms = np.zeros(6, np.float32)
     check(lib.nr_stage_times(h, _ptr(ms)), "nr_stage_times")
     return dict(march_ms=float(ms[0]), field_ms=float(ms[1]), composite_ms=float(ms[2]),
-                chunks=int(ms[3]), live_samples=int(ms[4]))
+                chunks=int(ms[3]), live_samples=int(ms[4]), bones_read_per_sample=float(ms[5]))
 
 
 def nr_launch_count() -> int:
     return int(lib.nr_launch_count())
+
+
+def nr_l2_gather_rate(device: int, table_bytes: int, load_bytes: int) -> float:
+    """Bytes per second of random L2-resident gathers of load_bytes (see include/nr.h)."""
+    v = C.c_double()
+    check(lib.nr_l2_gather_rate(int(device), int(table_bytes), int(load_bytes), C.byref(v)), "nr_l2_gather_rate")
+    return float(v.value)
 
 
 class _DevArray:

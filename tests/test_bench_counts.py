@@ -26,3 +26,13 @@ def test_counts_follow_the_subject():
     assert bench.field_bytes_per_sample(s, table_bytes=4) == 768 + 8 * 8 * 2 * 4 + 32
     s["res_enabled"] = 0
     assert bench.mlp_flops_per_sample(s) == 2 * (16 * 64 + 2 * 64 * 64 + 64 * 4)
+
+
+def test_counts_follow_the_feature_count():
+    # four features per level: the first canonical layer sees L x 4 inputs, each corner read is 4 x 2 B
+    s = dict(synth.config_frame512()["subject"])
+    s["hash_feats"] = 4
+    assert bench.field_bytes_per_sample(s, table_bytes=2) == 768 + 16 * 8 * 4 * 2 + 32
+    res = 39 * 64 + 64 * 64 + 64 * 64 + 103 * 64 + 64 * 3
+    can = 64 * 64 + 2 * 64 * 64 + 64 * 4
+    assert bench.mlp_flops_per_sample(s) == 2 * (res + can)

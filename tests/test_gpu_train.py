@@ -208,3 +208,49 @@ def test_patch_batch_with_weighted_mse():
     for g in ("wvol", "table", "mlp"):
         assert np.linalg.norm(ref[g]) > 0, g
         assert _rel(grads[g], ref[g]) <= 1e-4, (g, _rel(grads[g], ref[g]))
+
+
+def _per_tensor(flat, layers):
+    """Splits a flat master array [W1, b1, W2, b2, ...] into the tensors of `layers`."""
+    out, o = [], 0
+    for W, b in layers:
+        nW, nb = int(np.prod(np.shape(W))), int(np.prod(np.shape(b)))
+        out.append((flat[o:o + nW], flat[o + nW:o + nW + nb]))
+        o += nW + nb
+    assert o == flat.size
+    return out
+
+
+@pytest.mark.parametrize("last_std", [0.02, 0.0])
+def test_every_mlp_tensor_gradient_matches_oracle(last_std):
+    """Per weight matrix and bias vector, not per group: a group's norm is dominated by its
+    largest tensor (the residual MLP's output layer), so an error confined to an inner layer or
+    to the pose columns of residual layer 1 would hide under a group-level bound.  A non-zero
+    residual output layer gives every residual layer a gradient; a zero one (the initial state)
+    leaves gradient only on the output layer, which must then match alone.  (With a residual
+    whose offsets reach decimetres, float32-vs-float64 kink flips at the moved canonical points
+    put every residual tensor ~2 % off; the workloads' residuals stay at centimetres.)"""
+    subj = _smooth(synth.subject(35, hash_scale=0.5, res_last_std=last_std if last_std > 0 else None))
+    frames = synth.training_frames(36, 3, res=32)
+    for c in frames["cameras"]:
+        c.n_samples = 16
+    batch = synth.pixel_batch(37, 384, 3, 32, 32)
+    tgt = np.random.default_rng(38).uniform(0, 1, size=(384, 3)).astype(np.float32)
+    _, grads, _, _ = _gpu_step(subj, frames, batch, tgt, 16, 77, grad_only=True)
+    P = OF.Params(subj, requires_grad=True)
+    loss, _ = OR.train_loss(subj, P, frames, batch, tgt, 77, 16, np.zeros(3))
+    loss.backward()
+    g_dims = 3 + 6 * int(subj["res_pe_freqs"])
+    for name, layers, flat in (("res", P.res, grads["res"]), ("mlp", P.mlp, grads["mlp"])):
+        got = _per_tensor(flat, [(W.detach().numpy(), b.detach().numpy()) for W, b in layers])
+        for k, ((W, b), (gW, gb)) in enumerate(zip(layers, got)):
+            for what, ref, val in (("W", W.grad.numpy().ravel(), gW), ("b", b.grad.numpy().ravel(), gb)):
+                if np.linalg.norm(ref) == 0:
+                    assert np.abs(val).max() <= 1e-12, (name, k, what)
+                    continue
+                assert _rel(val, ref) <= 2e-3, (name, k + 1, what, _rel(val, ref))
+            if name == "res" and k == 0 and np.linalg.norm(W.grad.numpy()[:, g_dims:]) > 0:
+                # the pose columns (Omega joins layer 1 as a per-frame bias on the device)
+                ref = W.grad.numpy()[:, g_dims:].ravel()
+                val = gW.reshape(W.shape)[:, g_dims:].ravel()
+                assert _rel(val, ref) <= 2e-3, ("res pose columns", _rel(val, ref))

@@ -176,3 +176,24 @@ class _U32:
     def __init__(self, ptr):
         self.__cuda_array_interface__ = {"shape": (1,), "typestr": "<i4", "data": (ptr, False), "version": 3,
                                          "strides": None}
+
+
+def test_profiled_render_counts_the_bone_channels_read(frame_structured):
+    """A profiled render reports how many weight-volume channels the pipeline read per live
+    sample: at least one (a sample on the body), fewer than the 24 bones (support skipping),
+    and none reported by the mma.sync path, which does not count."""
+    nr = nrmod()
+    cfg = frame_structured
+    cam = _small(cfg["camera"], 96)
+    S = nr.Subject(cfg["subject"])
+    try:
+        S.set_pose(*cfg["pose"])
+        S.render(cam, nr.make_opts("bf16", "f16", True, 1e-4, profile=True))
+        st = S.stage_times()
+        S.render(cam, nr.make_opts("bf16", "f16", True, 1e-4, profile=True, mma_sync=True))
+        st_sync = S.stage_times()
+    finally:
+        S.close()
+    assert st["live_samples"] == st_sync["live_samples"] > 0
+    assert 1.0 <= st["bones_read_per_sample"] < 24.0, st
+    assert st_sync["bones_read_per_sample"] == 0.0

@@ -76,3 +76,32 @@ def test_adam_matches_torch():
         pt.grad = torch.tensor(g)
         opt.step()
     assert np.allclose(p, pt.detach().numpy(), atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("group", ["res", "mlp"])
+def test_directional_derivative_along_the_whole_gradient(group):
+    """The gradient of a whole MLP (every layer at once) against central differences of the
+    loss along its own direction: (L(p + e g/|g|) - L(p - e g/|g|)) / 2e = |g|.  The residual
+    MLP moves every sample's canonical point, so the loss is linear in its weights only for
+    small steps: at e = 1e-3 in parameter norm the difference quotient already has the wrong
+    sign; 1e-5 and 1e-6 are inside the linear range."""
+    subj, frames, batch, tgt = _setup()
+    P = OF.Params(subj, requires_grad=True)
+    loss, _ = OR.train_loss(subj, P, frames, batch, tgt, 99, 16, np.zeros(3))
+    loss.backward()
+    tens = [t for Wb in (P.res if group == "res" else P.mlp) for t in Wb]
+    g = [t.grad.clone() for t in tens]
+    nrm = float(torch.sqrt(sum((x ** 2).sum() for x in g)))
+    assert nrm > 0
+    for eps in (1e-5, 1e-6):
+        step = eps / nrm
+        with torch.no_grad():
+            for t, d in zip(tens, g):
+                t.add_(d, alpha=step)
+            lp = float(OR.train_loss(subj, P, frames, batch, tgt, 99, 16, np.zeros(3))[0])
+            for t, d in zip(tens, g):
+                t.add_(d, alpha=-2 * step)
+            lm = float(OR.train_loss(subj, P, frames, batch, tgt, 99, 16, np.zeros(3))[0])
+            for t, d in zip(tens, g):
+                t.add_(d, alpha=step)
+        assert abs((lp - lm) / (2 * eps) / nrm - 1.0) <= 1e-2, (group, eps, (lp - lm) / (2 * eps), nrm)
