@@ -60,9 +60,9 @@ def parse():
                    help="with --train-only: train the pose refiner and CNN_skel as well (patch batches)")
     p.add_argument("--train-layout", choices=["uniform", "patch"], default="uniform",
                    help="uniform random pixels, or 6 patches of 20x20 per image with MSE weight 0.2")
-    p.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving run (0 = skip)")
+    p.add_argument("--serve-seconds", type=float, default=30.0, help="length of the serving run (0 = skip)")
     p.add_argument("--serve-only", action="store_true", help="run only the serving scenario")
-    p.add_argument("--serve-slots", type=int, default=8, help="concurrent requests on the device (server slots)")
+    p.add_argument("--serve-slots", type=int, default=2, help="concurrent requests on the device (server slots)")
     p.add_argument("--no-sweep", dest="sweep", action="store_false", help="skip the precision sweep")
     p.add_argument("--sweep-only", action="store_true", help="run only the precision sweep")
     return p.parse_args()
@@ -305,7 +305,7 @@ def occupancy_bench(nr, device, mlp, steps=5):
             "live_samples_grid": statistics.mean(live_grid), "live_samples_no_skip": statistics.mean(live_full)}
 
 
-def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slots=16):
+def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slots=16, policy=None, baseline=True):
     """Multi-user serving: n_subjects frame-workload subjects resident on the device, Poisson
     arrivals at `rate` req/s for `duration` s, each request a random subject, a camera on the
     2.5 m sphere, a fresh pose (<= 30 deg per bone) and 256^2 / 512^2 / 1024^2 with probabilities
@@ -323,6 +323,8 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
         outs.append(arena[off:off + 4 * n])
         off += 4 * n
     srv = nr.Server(max_bytes=max_slots * (137 << 20), max_slots=max_slots, device=device)
+    if policy:
+        srv.set_policy(**policy)
     for S in subs:
         srv.add_subject(S)
     # warm-up: one request per resolution
@@ -347,7 +349,7 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
         by_res.setdefault(q["camera"].width, []).append(l)
     # one at a time through the plain path (service times), then a FIFO queue over the same arrivals
     service = []
-    for i, q in enumerate(reqs):
+    for i, q in enumerate(reqs if baseline else []):
         S = subs[q["subject"]]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -370,9 +372,9 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
             "p50_ms_by_res": {str(k): pct(v, 50) for k, v in sorted(by_res.items())},
             "p99_ms_by_res": {str(k): pct(v, 99) for k, v in sorted(by_res.items())},
             "rays_per_s": sum(sizes) / (t_end - t0), "peak_active": st["peak_active"], "slots": st["slots"],
-            "one_at_a_time": {"rays_per_s": sum(sizes) / (sum(service) / 1000.0),
-                              "p50_ms": pct(fifo, 50), "p99_ms": pct(fifo, 99),
-                              "mean_service_ms": float(np.mean(service))}}
+            "one_at_a_time": ({"rays_per_s": sum(sizes) / (sum(service) / 1000.0),
+                               "p50_ms": pct(fifo, 50), "p99_ms": pct(fifo, 99),
+                               "mean_service_ms": float(np.mean(service))} if baseline else None)}
 
 
 SWEEP_REFERENCE = os.path.join(ROOT, "tests", "golden", "sweep_oracle_pixels.txt")
@@ -492,8 +494,11 @@ def run_reference(a):
 # Per frame of the frame workload, from one ncu capture of the four field launches of a frame on
 # the default bf16 path, valid while the kernel sources have the SHA-256 given: DRAM bytes read +
 # written, and the bytes of the L1 sectors the global loads touched.
-FIELD_CAPTURE = {"sha256": None, "dram_bytes_per_frame": None, "l1_sector_bytes_per_frame": None,
-                 "live_samples_per_frame": None}
+FIELD_CAPTURE = {"sha256": "e33d92af34d0974e03c523122f2493723a6e09dad249e20c1add26d392a6c776",
+                 "dram_bytes_per_frame": 152495104 + 55798272,
+                 "l1_sector_bytes_per_frame": 474172770 * 32,
+                 "l2_bytes_per_frame": 4487798624,
+                 "live_samples_per_frame": 6173672}
 FIELD_SOURCES = ["field_ws.cu", "gather.cuh", "t5.cuh", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
 
@@ -701,9 +706,11 @@ def run_ours(a):
                          "counted": bytes_per_sample,
                          "l1_sector_bytes": (cap["l1_sector_bytes_per_frame"] / cap["live_samples_per_frame"]
                                              if cap else None),
+                         "l2_bytes": (cap["l2_bytes_per_frame"] / cap["live_samples_per_frame"] if cap else None),
                          "note": "counted: all 24 bone channels (768 B) + 16 hash levels (512 B) + sample in/out; "
-                                 "the kernel skips bone channels whose support misses the candidate and reads "
-                                 "L1 sectors of 32 B, so it moves a different number of bytes through L1"},
+                                 "the kernel skips bone channels whose support misses the candidate; every "
+                                 "4-byte corner read touches a 32-byte L1 sector (l1_sector_bytes), of which "
+                                 "l2_bytes miss L1 (ncu capture of these sources)"},
                      "vs_hbm": {"frac": achieved / hbm, "peak": hbm,
                                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
                      "traffic": cap["dram_bytes_per_frame"] if cap else None,

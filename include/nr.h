@@ -341,11 +341,31 @@ typedef struct {
 
 /* Creates a server on `device` with a device-memory budget for its slots
  * (each slot needs about 136 MiB) and a slot limit (1..256); starts its
- * worker thread.  Queued requests are dispatched smallest first (width x
- * height x n_samples), except that a request queued for 40 ms or more goes
- * first; requests of at most 512 x 512 pixels run on high-priority streams.
- * NR_EINVAL if max_bytes cannot hold one slot. */
+ * worker thread.  Queued requests are dispatched earliest deadline first
+ * (nr_server_set_policy changes the order).  Few slots serve the latency
+ * tail best (2 measured best at 240 req/s of the conferencing mix): every
+ * field launch occupies all SMs, so requests running side by side stretch
+ * one another.  NR_EINVAL if max_bytes cannot hold one slot. */
 nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t max_slots, nr_server **out);
+/* Dispatch policy of a server: the order in which queued requests are admitted
+ * into free slots, and whether small requests run on high-priority streams. */
+#define NR_SERVE_SMALLEST_FIRST 0u  /* fewest pixel x sample slots first; a request queued
+                                       age_ms or longer goes first (arrival order) */
+#define NR_SERVE_FIFO 1u            /* arrival order */
+#define NR_SERVE_EDF 2u             /* earliest deadline first, deadline = arrival + deadline_ms
+                                       + deadline_ms_per_mpixel x width x height / 1e6 */
+typedef struct {
+  uint32_t order;                 /* NR_SERVE_* (default NR_SERVE_EDF) */
+  float age_ms;                   /* smallest first: the aging bound (default 40) */
+  float deadline_ms;              /* EDF: the deadline's constant part (default 20) */
+  float deadline_ms_per_mpixel;   /* EDF: its part per megapixel (default 20) */
+  uint32_t priority_streams;      /* 1: requests of at most 512 x 512 pixels on high-priority
+                                     streams, the rest on low-priority ones; 0: all alike (default) */
+} nr_server_policy;
+/* Sets the dispatch policy (applies to requests dispatched afterwards).  NR_EINVAL for an
+ * unknown order or a negative time. */
+nr_status nr_server_set_policy(nr_server *srv, const nr_server_policy *policy);
+
 /* Registers a subject (not owned; it must outlive the server and must not be
  * trained or given new parameters while the server runs).  All subjects must
  * share one occupancy grid size. */

@@ -255,6 +255,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
   WsLayer *sLay = reinterpret_cast<WsLayer *>(sBar + 3 * kWsGroups);
   uint32_t *sTmem = reinterpret_cast<uint32_t *>(sLay + kWsMaxLayers);
 
+  {  // a block with no tile leaves before any set-up (the live count is known only here)
+    const uint32_t n0 = n_dev ? *n_dev : n_fixed;
+    if ((uint64_t)blockIdx.x * kWsGroups * 128 >= n0) return;
+  }
   const int tid = threadIdx.x, warp = tid >> 5;
   const bool res = P.res_enabled != 0;
   const int H = P.hidden;

@@ -7,11 +7,15 @@
 //     derived layouts stay resident on the device;
 //   * a request (subject, camera, pose, options, output buffer) is queued by
 //     nr_server_submit from any host thread;
-//   * one worker thread admits queued requests into slots, smallest first (fewest
-//     pixel x sample slots; a request queued longer than kAgeMs goes first, in
-//     arrival order), so that short frames are not stuck behind long ones.  A
-//     slot owns two CUDA streams (high priority for requests of at most
-//     kSmallPixels pixels, low priority for the rest), the request's pose buffers (bone transforms,
+//   * one worker thread admits queued requests into slots in the order of the
+//     server's policy (nr_server_set_policy): earliest deadline first (deadline
+//     = arrival + deadline_ms + deadline_ms_per_mpixel x megapixels, 20 ms +
+//     20 ms per megapixel by default), smallest first (fewest pixel x sample
+//     slots; a request queued longer than age_ms goes first), or first come
+//     first served.  Few slots serve the tail best: each field launch holds
+//     every SM, so requests running side by side stretch each other.  A
+//     slot owns two CUDA streams (with priority streams on: high priority for
+//     requests of at most kSmallPixels pixels, low priority for the rest), the request's pose buffers (bone transforms,
 //     folded residual bias, posed occupancy bitfield) and its sample queues.
 //     Slots are created on demand while the device-memory budget allows and are
 //     reused afterwards: admission is by memory and by slot count;
@@ -88,6 +92,7 @@ struct nr_server {
   bool stopping = false, worker_exit = false;
   std::thread worker;
   nr_server_stats st{};
+  nr_server_policy pol{NR_SERVE_EDF, (float)nr::kAgeMs, 20.f, 20.f, 0u};
 };
 
 namespace nr {
@@ -252,17 +257,34 @@ static void worker_main(nr_server *srv) {
       }
     }
     if (slot) {
-      // smallest first, unless the oldest request has waited kAgeMs
-      auto pick = srv->queue.begin();
-      const double oldest_ms =
-          std::chrono::duration<double, std::milli>(Clock::now() - srv->reqs[*pick].t_submit).count();
-      if (oldest_ms < kAgeMs) {
-        uint64_t best = UINT64_MAX;
+      auto pick = srv->queue.begin();   // the queue is in arrival order: first come first served
+      const nr_server_policy &pol = srv->pol;
+      if (pol.order == NR_SERVE_SMALLEST_FIRST) {
+        // smallest first, unless the oldest request has waited age_ms
+        const double oldest_ms =
+            std::chrono::duration<double, std::milli>(Clock::now() - srv->reqs[*pick].t_submit).count();
+        if (oldest_ms < pol.age_ms) {
+          uint64_t best = UINT64_MAX;
+          for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it) {
+            const nr_camera &c = srv->reqs[*it].r.cam;
+            const uint64_t work = (uint64_t)c.width * c.height * c.n_samples;
+            if (work < best) {
+              best = work;
+              pick = it;
+            }
+          }
+        }
+      } else if (pol.order == NR_SERVE_EDF) {
+        // earliest deadline first: arrival + deadline_ms + deadline_ms_per_mpixel x megapixels
+        double best = 1e300;
+        const Clock::time_point t0 = srv->reqs[*pick].t_submit;
         for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it) {
-          const nr_camera &c = srv->reqs[*it].r.cam;
-          const uint64_t work = (uint64_t)c.width * c.height * c.n_samples;
-          if (work < best) {
-            best = work;
+          const Request &q = srv->reqs[*it];
+          const double mpix = (double)q.r.cam.width * q.r.cam.height * 1e-6;
+          const double due = std::chrono::duration<double, std::milli>(q.t_submit - t0).count() + pol.deadline_ms +
+                             pol.deadline_ms_per_mpixel * mpix;
+          if (due < best) {
+            best = due;
             pick = it;
           }
         }
@@ -270,7 +292,9 @@ static void worker_main(nr_server *srv) {
       const uint64_t id = *pick;
       srv->queue.erase(pick);
       Request &q = srv->reqs[id];
-      slot->cur = (uint64_t)q.r.cam.width * q.r.cam.height <= kSmallPixels ? slot->stream : slot->stream_lo;
+      slot->cur = (srv->pol.priority_streams && (uint64_t)q.r.cam.width * q.r.cam.height <= kSmallPixels)
+                      ? slot->stream
+                      : slot->stream_lo;
       q.state = 1;
       slot->busy = true;
       slot->req = id;
@@ -319,6 +343,18 @@ extern "C" nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t m
   srv->max_slots = max_slots;
   srv->worker = std::thread(worker_main, srv);
   *out = srv;
+  return NR_OK;
+}
+
+extern "C" nr_status nr_server_set_policy(nr_server *srv, const nr_server_policy *policy) {
+  NR_REQUIRE(server_ok(srv) && policy, "nr_server_set_policy: bad argument");
+  NR_REQUIRE(policy->order == NR_SERVE_SMALLEST_FIRST || policy->order == NR_SERVE_FIFO ||
+                 policy->order == NR_SERVE_EDF,
+             "nr_server_set_policy: unknown order %u", policy->order);
+  NR_REQUIRE(policy->age_ms >= 0.f && policy->deadline_ms >= 0.f && policy->deadline_ms_per_mpixel >= 0.f,
+             "nr_server_set_policy: negative time");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  srv->pol = *policy;
   return NR_OK;
 }
 

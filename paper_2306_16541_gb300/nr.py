@@ -37,6 +37,7 @@ NR_RENDER_TCGEN05 = 2
 NR_RENDER_MMA2 = 4
 NR_RENDER_F32_TC = 16
 NR_RENDER_MMA_SYNC = 32
+NR_SERVE_SMALLEST_FIRST, NR_SERVE_FIFO, NR_SERVE_EDF = 0, 1, 2
 NR_ABI_VERSION = 1
 
 _fp = C.POINTER(C.c_float)
@@ -84,6 +85,11 @@ class nr_request(C.Structure):
                 ("root_t", C.c_float * 3), ("opts", nr_render_opts), ("out_rgba", C.c_void_p)]
 
 
+class nr_server_policy(C.Structure):
+    _fields_ = [("order", C.c_uint32), ("age_ms", C.c_float), ("deadline_ms", C.c_float),
+                ("deadline_ms_per_mpixel", C.c_float), ("priority_streams", C.c_uint32)]
+
+
 class nr_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("rejected", C.c_uint64), ("active", C.c_uint32), ("queued", C.c_uint32),
@@ -120,6 +126,7 @@ def _load() -> C.CDLL:
         "nr_l2_gather_rate": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)], C.c_int),
         "nr_server_create": ([C.c_int, C.c_uint64, C.c_uint32, C.POINTER(vp)], C.c_int),
         "nr_server_add_subject": ([vp, vp, C.POINTER(C.c_uint32)], C.c_int),
+        "nr_server_set_policy": ([vp, C.POINTER(nr_server_policy)], C.c_int),
         "nr_server_submit": ([vp, C.POINTER(nr_request), C.POINTER(C.c_uint64)], C.c_int),
         "nr_server_poll": ([vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
         "nr_server_wait": ([vp, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)], C.c_int),
@@ -528,6 +535,12 @@ class Server:
         self.h = C.c_void_p()
         check(lib.nr_server_create(device, int(max_bytes), int(max_slots), C.byref(self.h)), "nr_server_create")
         self.subjects = []
+
+    def set_policy(self, order: int = NR_SERVE_EDF, age_ms: float = 40.0, deadline_ms: float = 20.0,
+                   deadline_ms_per_mpixel: float = 20.0, priority_streams: bool = False) -> None:
+        p = nr_server_policy(int(order), float(age_ms), float(deadline_ms), float(deadline_ms_per_mpixel),
+                             int(bool(priority_streams)))
+        check(lib.nr_server_set_policy(self.h, C.byref(p)), "nr_server_set_policy")
 
     def add_subject(self, subject: Subject) -> int:
         idx = C.c_uint32()

@@ -82,7 +82,8 @@ def test_binding_constants_match_header(nr):
     assert not wrong, wrong
 
 
-STRUCTS = ["nr_subject_desc", "nr_camera", "nr_render_opts", "nr_train_batch", "nr_request", "nr_server_stats"]
+STRUCTS = ["nr_subject_desc", "nr_camera", "nr_render_opts", "nr_train_batch", "nr_request", "nr_server_stats",
+           "nr_server_policy"]
 
 
 def test_struct_layouts_match_header(nr, tmp_path):
@@ -156,3 +157,10 @@ def test_option_and_camera_marshalling(nr):
     assert (c.fx, c.fy) == (80.0, 80.0) and (c.t_near, c.t_far) == (1.5, 3.5)
     assert np.allclose(np.array(c.R[:]), np.asarray(cam.R, np.float32).ravel())
     assert np.allclose(np.array(c.t[:]), np.asarray(cam.t, np.float32).ravel())
+
+
+def test_server_policy_refused_without_a_server(nr):
+    """nr_server_set_policy validates its handle before touching a server (no device needed)."""
+    pol = nr.nr_server_policy(nr.NR_SERVE_EDF, 40.0, 20.0, 20.0, 0)
+    assert nr.lib.nr_server_set_policy(None, C.byref(pol)) == nr.NR_EINVAL
+    assert b"nr_server_set_policy" in nr.lib.nr_last_error()

@@ -34,11 +34,16 @@ def _requests(n, seed):
     return out
 
 
-def test_mix_equals_alone(subjects):
+@pytest.mark.parametrize("order", ["edf", "smallest_first", "fifo"])
+def test_mix_equals_alone(subjects, order):
+    """Under every dispatch policy each request of the mix equals the same request rendered
+    alone, bit for bit (bf16 requests on the tcgen05 pipeline included)."""
     nr = nrmod()
     subs = [nr.Subject(s) for s in subjects]
     srv = nr.Server(max_bytes=8 << 30, max_slots=6)
     try:
+        srv.set_policy(order={"edf": nr.NR_SERVE_EDF, "smallest_first": nr.NR_SERVE_SMALLEST_FIRST,
+                              "fifo": nr.NR_SERVE_FIFO}[order], priority_streams=(order == "smallest_first"))
         for s in subs:
             srv.add_subject(s)
         reqs = _requests(30, 1)
