@@ -361,10 +361,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       tm_st8(my + kWsOne, c);
     }
     const int n_layers = (res ? 5 : 0) + H + 1;
+    bool nx_valid = false;
     // this thread's sample of a tile: position and spacing (zero beyond n)
     auto load_in = [&](uint32_t t, LbsState &st, float &dl) {
       const uint32_t jj = t * 128 + r;
       st.x0 = st.x1 = st.x2 = dl = 0.f;
+      nx_valid = jj < n;
       if (jj < n) {
         if (MODE == kModeRender) {
           const float4 v = in[jj];
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
     float d_next = 0.f;
     if (tile < n_tiles) {
       load_in(tile, nx, d_next);
-      lbs_begin(P, sG, sBox, nx);
+      lbs_begin(P, sG, sBox, nx, nx_valid);
     }
     for (; tile < n_tiles; tile += tstride) {
       const uint32_t j = tile * 128 + r;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       auto overlap = [&]() {
         if (!more) return;
         if (stage == 0)
-          lbs_begin(P, sG, sBox, nx);
+          lbs_begin(P, sG, sBox, nx, nx_valid);
         else
           lbs_round(P, sG, nx);
         ++stage;
@@ -414,16 +416,25 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
         const float h1 = (s1 - P.box_c[1]) * P.box_ih[1];
         const float h2 = (s2 - P.box_c[2]) * P.box_ih[2];
         gm[0] = h0; gm[1] = h1; gm[2] = h2;
+        // band 0 from sincospif, band k + 1 from band k by the double-angle identities
+        // sin 2a = 2 sin a cos a, cos 2a = (cos a - sin a)(cos a + sin a); the absolute error at
+        // most doubles per band (below 1e-5 at band 5, against the 2^-9 of the bf16/f16 operand)
+        float sa, ca, sb, cb, sd, cd;
+        sincospif(h0, &sa, &ca);
+        sincospif(h1, &sb, &cb);
+        sincospif(h2, &sd, &cd);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const float sc = (float)(1 << k);
-          float sa, ca, sb, cb, sd, cd;
-          sincospif(sc * h0, &sa, &ca);
-          sincospif(sc * h1, &sb, &cb);
-          sincospif(sc * h2, &sd, &cd);
           const float w = (k < P.res_freqs) ? P.hann[k] : 0.f;
           gm[3 + 6 * k + 0] = w * sa; gm[3 + 6 * k + 1] = w * sb; gm[3 + 6 * k + 2] = w * sd;
           gm[3 + 6 * k + 3] = w * ca; gm[3 + 6 * k + 4] = w * cb; gm[3 + 6 * k + 5] = w * cd;
+          if (k < 5) {
+            const float na = 2.f * sa * ca, nb = 2.f * sb * cb, nd = 2.f * sd * cd;
+            ca = (ca - sa) * (ca + sa);
+            cb = (cb - sb) * (cb + sb);
+            cd = (cd - sd) * (cd + sd);
+            sa = na; sb = nb; sd = nd;
+          }
         }
         gm[39] = 1.f;                                       // against the weights' bias columns
         gm[40] = 1.f;

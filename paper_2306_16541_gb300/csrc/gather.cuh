@@ -44,8 +44,8 @@ __device__ __forceinline__ void bone_point(const FieldParams &P, const float *__
 }
 
 // lbs_warp with the corner blocks of four bones loaded together, as a resumable computation so
-// that a kernel can spread it over waits for other work: lbs_begin takes every candidate's
-// support-box test (no loads); the bones kept by any lane of the warp are then visited four at a
+// that a kernel can spread it over waits for other work: lbs_begin takes the candidates'
+// support-box tests (no loads); the bones kept by any lane of the warp are then visited four at a
 // time by lbs_round -- the same bones in every lane, so the pose reads stay broadcasts -- with
 // each lane's loads predicated on its own test, and folded into (sum, n) in increasing bone
 // order; lbs_end forms x_skel and S.  A bone that no lane keeps is skipped by all (as lbs_warp
@@ -57,17 +57,60 @@ struct LbsState {
   float n0, n1, n2, sum;
 };
 
+// Margin, in voxels, of the warp-level candidate test below: far above the float32 rounding of
+// the transformed points (about 1e-5 voxel).
+constexpr float kCandMargin = 0.0625f;
+
+// lbs_begin's support-box test, taken only for the bones whose box can meet one of the warp's
+// samples.  The valid samples of the warp lie in an axis-aligned box of centre c and half
+// extents e; its image under bone i's transform [R_i | t_i] lies in the box of centre G_i c and
+// half extents |R_i| e (componentwise absolute values), so a bone whose support box misses that
+// box, widened by kCandMargin, is kept by no lane: lane i < 24 takes bone i's test, and the
+// exact per-sample tests run over the bones that pass (the same tests, so the kept bones are the
+// same).  A lane without a sample (valid false) keeps no bone.  Warp-collective.
 __device__ __forceinline__ void lbs_begin(const FieldParams &P, const float *__restrict__ sG,
-                                          const float *__restrict__ sBox, LbsState &st) {
-  uint32_t mine = (1u << kBones) - 1u;
+                                          const float *__restrict__ sBox, LbsState &st, bool valid) {
+  uint32_t mine = valid ? (1u << kBones) - 1u : 0u;
   if (sBox) {
     mine = 0u;
+    float lo0 = valid ? st.x0 : INFINITY, lo1 = valid ? st.x1 : INFINITY, lo2 = valid ? st.x2 : INFINITY;
+    float hi0 = valid ? st.x0 : -INFINITY, hi1 = valid ? st.x1 : -INFINITY, hi2 = valid ? st.x2 : -INFINITY;
 #pragma unroll
-    for (int i = 0; i < kBones; ++i) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+      lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+      lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+      hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+      hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+      hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+    }
+    uint32_t cand = 0u;
+    if (lo0 <= hi0) {   // some lane has a sample (warp-uniform)
+      const int lane = threadIdx.x & 31;
+      bool hit = false;
+      if (lane < kBones) {
+        const float c0 = 0.5f * (lo0 + hi0), c1 = 0.5f * (lo1 + hi1), c2 = 0.5f * (lo2 + hi2);
+        const float e0 = 0.5f * (hi0 - lo0), e1 = 0.5f * (hi1 - lo1), e2 = 0.5f * (hi2 - lo2);
+        const float *g = sG + 12 * lane;
+        float p0, p1, p2, u0, u1, u2;
+        bone_point(P, g, c0, c1, c2, p0, p1, p2, u0, u1, u2);
+        const float r0 = (fabsf(g[0]) * e0 + fabsf(g[1]) * e1 + fabsf(g[2]) * e2) * P.vol_scale[0] + kCandMargin;
+        const float r1 = (fabsf(g[4]) * e0 + fabsf(g[5]) * e1 + fabsf(g[6]) * e2) * P.vol_scale[1] + kCandMargin;
+        const float r2 = (fabsf(g[8]) * e0 + fabsf(g[9]) * e1 + fabsf(g[10]) * e2) * P.vol_scale[2] + kCandMargin;
+        const float *b = sBox + 6 * lane;
+        hit = u0 + r0 >= b[0] && u1 + r1 >= b[1] && u2 + r2 >= b[2] && u0 - r0 < b[3] && u1 - r1 < b[4] &&
+              u2 - r2 < b[5];
+      }
+      cand = __ballot_sync(0xffffffffu, hit);
+    }
+#pragma unroll 1
+    while (cand) {
+      const int i = __ffs(cand) - 1;
+      cand &= cand - 1u;
       float p0, p1, p2, ux, uy, uz;
       bone_point(P, sG + 12 * i, st.x0, st.x1, st.x2, p0, p1, p2, ux, uy, uz);
       const float *b = sBox + 6 * i;
-      const bool keep = !(ux < b[0] || uy < b[1] || uz < b[2] || ux >= b[3] || uy >= b[4] || uz >= b[5]);
+      const bool keep = valid && !(ux < b[0] || uy < b[1] || uz < b[2] || ux >= b[3] || uy >= b[4] || uz >= b[5]);
       mine |= (uint32_t)keep << i;
     }
   }
