@@ -4,14 +4,15 @@
 // wait on other work (the tcgen05 pipeline of field_ws.cu) cannot hide one
 // L2 round trip per bone and per level behind other warps.
 //
-// The arithmetic and its order are those of lbs_warp and hash_level in
-// field.cuh, so the results are bitwise the same:
 //   - inverse LBS: the bones kept anywhere in the warp four at a time, their
 //     kept corner blocks loaded together and folded into (sum, n) in
-//     increasing bone order;
+//     increasing bone order -- the arithmetic and order of lbs_warp in
+//     field.cuh, so x_skel and S are bitwise the same;
 //   - hash encoding (f16 table): the dense levels' corner blocks and the hashed
-//     levels' corners read four levels at a time, each level's two features
-//     summed over its eight corners in corner order.
+//     levels' corners read four levels at a time; each level's two features
+//     interpolated as nested lerps on the packed f16 pairs (x, then y, then z),
+//     whose rounding (2^-11 relative per step) stays below that of the bf16 /
+//     f16 MLP operand the pair becomes.
 #pragma once
 
 #include "field.cuh"
@@ -209,18 +210,31 @@ __device__ __forceinline__ void level_load(const FieldParams &P, int l, const Le
   }
 }
 
-// Trilinear sum of a level's two features over its corners, in corner order.
+// Packed f16 pair lerp a + f (b - a), both halves.
+__device__ __forceinline__ uint32_t lerp_h2(uint32_t a, uint32_t b, uint32_t f) {
+  uint32_t d;
+  asm("{\n.reg .b32 t;\nsub.rn.f16x2 t, %2, %1;\nfma.rn.f16x2 %0, %3, t, %1;\n}\n" : "=r"(d) : "r"(a), "r"(b), "r"(f));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t f16x2_bcast(float f) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %1;" : "=r"(d) : "f"(f));
+  return d;
+}
+
+// A level's two features at the point: trilinear interpolation of the eight packed corners as
+// seven packed lerps, then the pair in the MLP's operand type (0 outside the box).
 template <typename T>
 __device__ __forceinline__ uint32_t level_sum(const LevelCell &c, const uint32_t (&v)[8], bool inside) {
-  float fa = 0.f, fb = 0.f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const float w = ((k & 1) ? c.f0 : 1.f - c.f0) * (((k >> 1) & 1) ? c.f1 : 1.f - c.f1) * ((k >> 2) ? c.f2 : 1.f - c.f2);
-    const float2 f = h2f2(v[k]);
-    fa = fmaf(w, f.x, fa);
-    fb = fmaf(w, f.y, fb);
-  }
-  return inside ? pack2<T>(fa, fb) : 0u;
+  const uint32_t fx = f16x2_bcast(c.f0), fy = f16x2_bcast(c.f1), fz = f16x2_bcast(c.f2);
+  const uint32_t a = lerp_h2(v[0], v[1], fx), b = lerp_h2(v[2], v[3], fx);
+  const uint32_t e = lerp_h2(v[4], v[5], fx), g = lerp_h2(v[6], v[7], fx);
+  const uint32_t r = lerp_h2(lerp_h2(a, b, fy), lerp_h2(e, g, fy), fz);
+  if (!inside) return 0u;
+  if (TcFmt<T>::value == 0) return r;
+  const float2 f = h2f2(r);
+  return pack2<T>(f.x, f.y);
 }
 
 // Levels l .. l + NL - 1 (each dense or hashed; the levels below n_dense are dense): every corner
