@@ -400,7 +400,8 @@ def sweep_reference() -> dict:
 def sweep_bench(nr, device):
     """Precision sweep: 1920x1080, 192 samples per ray, the tiny workload's field with 2^20
     entries per level (and a textured variant), no occupancy.  Every MLP tier (f32 on CUDA
-    cores, f32_tc = float32 accuracy on the tensor cores, bf16, f16, fp8) x hash-feature tier
+    cores, f32_tc = float32 accuracy on the tensor cores, bf16, f16, fp8 on the default tcgen05
+    pipeline, fp8_sync = fp8 on warp-level mma.sync) x hash-feature tier
     (f32, f16): rays/s (CUDA events), PSNR, max-abs and per-pixel error percentiles against the
     FP64 oracle's values at seeded pixels (stored by tests/golden/make_sweep_reference.py), and
     PSNR against the f32 GPU image."""
@@ -420,9 +421,10 @@ def sweep_bench(nr, device):
         img = torch.empty(cam.height, cam.width, 4, device="cuda")
         base = None
         rows = []
-        for mlp in ("f32", "f32_tc", "bf16", "f16", "fp8"):
+        for mlp in ("f32", "f32_tc", "bf16", "f16", "fp8", "fp8_sync"):
             for feat in ("f32", "f16"):
-                opts = nr.make_opts("f32" if mlp == "f32_tc" else mlp, feat, False, 0.0, f32_tc=mlp == "f32_tc")
+                dtype = {"f32_tc": "f32", "fp8_sync": "fp8"}.get(mlp, mlp)
+                opts = nr.make_opts(dtype, feat, False, 0.0, f32_tc=mlp == "f32_tc", mma_sync=mlp == "fp8_sync")
                 S.render(cam, opts, img)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

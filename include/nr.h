@@ -435,12 +435,14 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
                                  that small change S by at most 2.4e-6); training never skips. */
 #define NR_RENDER_MMA_SYNC 32u /* nr_render_opts.flags: bf16/f16 MLPs as warp-level mma.sync m16n8k16 over
                                  one 16-row tile per weight-fragment read (20 warps/SM, activations in
-                                 registers) instead of the default pipeline.
-                                 The default for NR_BF16 / NR_F16 is the warp-specialised tcgen05
-                                 pipeline: per SM four 128-sample tiles in flight, both MLPs as M = 128
-                                 MMAs with the activations in tensor memory, one issuing warp per tile.
-                                 Its waits are bounded; a wait that gives up makes the call return
-                                 NR_ETIMEOUT (the same holds for NR_RENDER_TCGEN05). */
+                                 registers), fp8 MLPs as mma.sync m16n8k32 with the activations
+                                 requantised through shared memory, instead of the default pipeline.
+                                 The default for NR_BF16 / NR_F16 / NR_FP8E4M3 is the warp-specialised
+                                 tcgen05 pipeline: per SM four 128-sample tiles in flight, both MLPs as
+                                 M = 128 MMAs (kind::f16, or kind::f8f6f4 with the same per-matrix and
+                                 per-input scales) with the activations in tensor memory, one issuing
+                                 warp per tile.  Its waits are bounded; a wait that gives up makes the
+                                 call return NR_ETIMEOUT (the same holds for NR_RENDER_TCGEN05). */
 #define NR_RENDER_F32_TC 16u  /* nr_render_opts.flags with mlp_dtype NR_F32 (nr_render, nr_query):
                                  both MLPs as warp-level tensor-core layers at float32 accuracy
                                  (each product as three TF32 products of hi/lo parts) instead of

@@ -22,6 +22,10 @@ constexpr int kMlpIn = 32;          // canonical MLP input (hash features, zero-
 constexpr int kMaxLevels = 16;
 constexpr int kResGammaPad = 48;    // 3 + 6 * 6 = 39 PE dims, padded to a multiple of 16
 constexpr int kMaxHidden = 4;
+// Slots of the fp8 tier's scale array read by the tcgen05 pipeline (written by field_fp8.cu):
+// 1 / s_a of gamma and of the hash encoding, residual layer 4's common multiplier, then per layer
+// of the pipeline's table the multiplier s_w s_a and the next input's 1 / s_a.
+constexpr int kF8SlotInvGam = 28, kF8SlotInvEnc = 29, kF8SlotC4 = 30, kF8SlotWs = 32;
 constexpr float kEpsW = 1e-4f;      // floor of the LBS denominator
 
 void set_error(const char *fmt, ...);
@@ -98,6 +102,7 @@ struct FieldParams {
   const uint8_t *fp8_blob;           // e4m3 weight blob (field_fp8.cu)
   const float *fp8_scales;           // its weight and activation scales
   const uint8_t *t5_bf16, *t5_f16;   // swizzled K-major weight blobs of the tcgen05 path (field_t5.cu)
+  const uint8_t *t5_fp8;             // the same layout in e4m3 with the fp8 tier's scales (field_fp8.cu)
   uint32_t *t5_err;                  // set by the tcgen05 path when a bounded wait gives up
   const float *bone_box;             // [24][6] per-bone support box in volume-index units, or NULL
   // occupancy from the field's density (kModeDensity / kModePose of the FP32 kernel)
@@ -165,7 +170,7 @@ struct nr_subject {
   void *fp8_jobs = nullptr;
   float *fp8_G = nullptr;
   bool fp8_ready = false;
-  uint8_t *t5_bf16 = nullptr, *t5_f16 = nullptr;
+  uint8_t *t5_bf16 = nullptr, *t5_f16 = nullptr, *t5_fp8 = nullptr;
   uint32_t *t5_err = nullptr;
   bool t5_ready = false;
   // current pose

@@ -16,6 +16,7 @@
 #include "field.cuh"
 #include "mma.cuh"
 #include "render.cuh"
+#include "t5.cuh"
 
 namespace nr {
 
@@ -451,13 +452,63 @@ __global__ void finish_scales_kernel(float *__restrict__ scales, int first, int 
   if (i < count) scales[first + i] = fmaxf(2.f * scales[first + i], 1e-20f) / kE4M3Max;
 }
 
+// ------------------------------------------- the tcgen05 pipeline's e4m3 operands
+// field_ws.cu runs the fp8 tier with the same scales: layer inputs x_q = e4m3(x / s_a), weights
+// in the swizzled K-major layout of the bf16 blob (t5_layout, 1-byte elements), and per layer a
+// multiplier m = s_w s_a and the next input's 1 / s_a.  Residual layer 4 accumulates its h3 and
+// gamma blocks in one product, so both blocks share one multiplier
+// c = max(s_w,h3 s_a,h3, s_w,gamma s_a,gamma): its weights are stored as e4m3(W s_a / c), whose
+// largest entry is at most 448.
+
+__global__ void fp8_ws_scales_kernel(float *__restrict__ sc, int res, int hidden) {
+  if (threadIdx.x != 0) return;
+  const float c4 = fmaxf(sc[SW_R4H] * sc[SA_RH3], sc[SW_R4G] * sc[SA_GAM]);
+  sc[kF8SlotC4] = c4;
+  sc[kF8SlotInvGam] = 1.f / sc[SA_GAM];
+  sc[kF8SlotInvEnc] = 1.f / sc[SA_ENC];
+  int li = 0;
+  auto put = [&](float m, float inv_next) {
+    sc[kF8SlotWs + 2 * li] = m;
+    sc[kF8SlotWs + 2 * li + 1] = inv_next;
+    ++li;
+  };
+  if (res) {
+    put(sc[SW_R1] * sc[SA_GAM], 1.f / sc[SA_RH1]);
+    put(sc[SW_R2] * sc[SA_RH1], 1.f / sc[SA_RH2]);
+    put(sc[SW_R3] * sc[SA_RH2], 1.f / sc[SA_RH3]);
+    put(c4, 1.f / sc[SA_RH4]);
+    put(sc[SW_R5] * sc[SA_RH4], 1.f);
+  }
+  put(sc[SW_C0] * sc[SA_ENC], 1.f / sc[SA_CH1]);
+  for (int l = 0; l + 1 < hidden; ++l) put(sc[SW_CH0 + l] * sc[SA_CH1 + l], 1.f / sc[SA_CH1 + l + 1]);
+  put(sc[SW_CL] * sc[SA_CH1 + hidden - 1], 1.f);
+}
+
+// One block per matrix: rows [out][n_in] of W times f = (num < 0 ? 1 : sc[num]) / sc[den] in
+// e4m3, into the 128-byte swizzled rows at byte offset dst (the blob is zeroed first).
+struct T5QuantJob {
+  const float *W;
+  int stride, col0, n_in, out, dst, num, den;
+};
+
+__global__ void quantize_t5_fp8_kernel(const T5QuantJob *__restrict__ jobs, const float *__restrict__ sc,
+                                       uint8_t *__restrict__ blob) {
+  const T5QuantJob J = jobs[blockIdx.x];
+  const float f = (J.num < 0 ? 1.f : sc[J.num]) / sc[J.den];
+  for (int i = threadIdx.x; i < J.out * J.n_in; i += blockDim.x) {
+    const int r = i / J.n_in, k = i % J.n_in;
+    blob[J.dst + r * 128 + ((((k >> 4) ^ (r & 7))) << 4) + (k & 15)] =
+        to_e4m3(J.W[(size_t)r * J.stride + J.col0 + k] * f);
+  }
+}
+
 nr_status prepare_fp8(nr_subject *s, cudaStream_t st) {
   if (s->fp8_ready) return NR_OK;
   const Fp8Layout fl = fp8_layout((int)s->hidden);
   if (!s->fp8_blob) {
     NR_CHECK_CUDA(cudaMalloc(&s->fp8_blob, (size_t)fl.total));
     NR_CHECK_CUDA(cudaMalloc(&s->fp8_scales, sizeof(float) * 64));
-    NR_CHECK_CUDA(cudaMalloc(&s->fp8_jobs, sizeof(QuantJob) * 16));
+    NR_CHECK_CUDA(cudaMalloc(&s->fp8_jobs, sizeof(QuantJob) * 16 + sizeof(T5QuantJob) * 16));
     NR_CHECK_CUDA(cudaMalloc(&s->fp8_G, sizeof(float) * (kBones * 12 + kWidth)));
   }
   const MasterOffsets m = master_offsets(s);
@@ -496,8 +547,32 @@ nr_status prepare_fp8(nr_subject *s, cudaStream_t st) {
   calibrate_kernel<<<kCalPoints / kCalThreads, kCalThreads, smem, st>>>(P, s->fp8_G + kBones * 12,
                                                                         s->fp8_scales);
   finish_scales_kernel<<<1, 32, 0, st>>>(s->fp8_scales, SA_GAM, kFp8Scales - SA_GAM);
+  // the tcgen05 pipeline's operands (allocated with the subject)
+  const T5Layout L = t5_layout(H);
+  if (!s->t5_fp8) {
+    set_error("tcgen05 fp8 weight blob missing");
+    return NR_ESTATE;
+  }
+  fp8_ws_scales_kernel<<<1, 32, 0, st>>>(s->fp8_scales, s->res_enabled ? 1 : 0, H);
+  NR_CHECK_CUDA(cudaMemsetAsync(s->t5_fp8, 0, (size_t)L.total, st));
+  std::vector<T5QuantJob> tj;
+  auto addq = [&](const float *W, int stride, int col0, int n_in, int out, int dst, int num, int den) {
+    tj.push_back(T5QuantJob{W, stride, col0, n_in, out, dst, num, den});
+  };
+  addq(s->res + m.r[0], g + P3, 0, g, kWidth, L.r1, -1, SW_R1);
+  addq(s->res + m.r[1], kWidth, 0, kWidth, kWidth, L.r2, -1, SW_R2);
+  addq(s->res + m.r[2], kWidth, 0, kWidth, kWidth, L.r3, -1, SW_R3);
+  addq(s->res + m.r[3], kWidth + g, 0, kWidth, kWidth, L.r4h, SA_RH3, kF8SlotC4);
+  addq(s->res + m.r[3], kWidth + g, kWidth, g, kWidth, L.r4g, SA_GAM, kF8SlotC4);
+  addq(s->res + m.r[4], kWidth, 0, kWidth, 3, L.r5, -1, SW_R5);
+  addq(s->mlp + m.c[0], (int)s->mlp_in, 0, (int)s->mlp_in, kWidth, L.c0, -1, SW_C0);
+  for (int l = 1; l < H; ++l) addq(s->mlp + m.c[l], kWidth, 0, kWidth, kWidth, L.ch[l - 1], -1, SW_CH0 + l - 1);
+  addq(s->mlp + m.c[H], kWidth, 0, kWidth, 4, L.cl, -1, SW_CL);
+  T5QuantJob *djobs = reinterpret_cast<T5QuantJob *>(static_cast<QuantJob *>(s->fp8_jobs) + 16);
+  NR_CHECK_CUDA(cudaMemcpyAsync(djobs, tj.data(), sizeof(T5QuantJob) * tj.size(), cudaMemcpyHostToDevice, st));
+  quantize_t5_fp8_kernel<<<(unsigned)tj.size(), 256, 0, st>>>(djobs, s->fp8_scales, s->t5_fp8);
   NR_CHECK_CUDA(cudaGetLastError());
-  count_launches(3);
+  count_launches(5);
   s->fp8_ready = true;
   return NR_OK;
 }

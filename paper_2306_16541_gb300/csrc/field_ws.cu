@@ -57,6 +57,7 @@ constexpr uint32_t kWsAcc = 0, kWsAct = 64, kWsOne = 96, kWsGam = 104;
 constexpr int kWsBiasTile = 64 * 128;     // bytes of one bias tile: 64 rows of one swizzled 128-byte row
 constexpr int kWsMaxLayers = 5 + kMaxHidden + 1;
 constexpr unsigned long long kWsTimeoutNs = 500000000ull;
+constexpr int kWsF8Inv = kWsMaxLayers * (1 + 64);   // fp8 tier: offset of 1 / s_a (gamma, encoding) in its table
 
 // One layer as the issuing thread sends it: nk K-steps of A (TMEM column a_col) x B (weights at
 // byte offset b_off of the shared blob), then nk2 K-steps of a second pair into the same
@@ -95,13 +96,49 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
 
-// D[128 x N] (+)= A[128 x 16] B^T with A in TMEM (columns a .. a + 7) and B in shared memory.
+// The fp8 tier's operand type: e4m3 operands of tcgen05.mma kind::f8f6f4 (format code 0).
+struct E4M3 {};
+template <>
+struct TcFmt<E4M3> {
+  static constexpr int value = 0;
+};
+template <typename T>
+constexpr bool kIsF8 = false;
+template <>
+constexpr bool kIsF8<E4M3> = true;
+
+// D[128 x N] (+)= A[128 x K] B^T with A in TMEM (columns a .. a + 7: K = 16 bf16/f16 or 32 e4m3
+// values) and B in shared memory.
+template <bool F8>
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
+  if constexpr (F8)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Four float32 values as e4m3 bytes 0..3 of a word (rounded, saturated to +-448; with ReLU when
+// RELU).
+template <bool RELU>
+__device__ __forceinline__ uint32_t e4m3x4(float a0, float a1, float a2, float a3) {
+  uint32_t d;
+  if constexpr (RELU)
+    asm("{\n.reg .b16 lo, hi;\ncvt.rn.satfinite.relu.e4m3x2.f32 lo, %2, %1;\n"
+        "cvt.rn.satfinite.relu.e4m3x2.f32 hi, %4, %3;\nmov.b32 %0, {lo, hi};\n}\n"
+        : "=r"(d) : "f"(a0), "f"(a1), "f"(a2), "f"(a3));
+  else
+    asm("{\n.reg .b16 lo, hi;\ncvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n"
+        "cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\nmov.b32 %0, {lo, hi};\n}\n"
+        : "=r"(d) : "f"(a0), "f"(a1), "f"(a2), "f"(a3));
+  return d;
 }
 
 // 32 columns of this warp's 32 lanes; the wait carries the registers so that no use of
@@ -182,6 +219,7 @@ __device__ __forceinline__ void ws_layer(const WsGroup &G, uint32_t &phase, bool
 // The issuer of one group: for each of its n layer steps, wait (bounded) for the group's input,
 // send the layer's MMAs and commit them; then commit once more and wait until every MMA it issued
 // has completed.  One thread.
+template <bool F8>
 __device__ __forceinline__ void ws_issue(uint32_t slot, uint32_t a_bar, uint32_t d_bar, uint32_t drain,
                                          const WsLayer *__restrict__ lay, int n_layers, uint32_t n_steps,
                                          const uint8_t *sW, uint32_t *err) {
@@ -195,10 +233,11 @@ __device__ __forceinline__ void ws_issue(uint32_t slot, uint32_t a_bar, uint32_t
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const WsLayer &Ly = lay[i % (uint32_t)n_layers];
     const uint64_t db = t5_desc(smem_u32(sW + Ly.b_off));
-    for (uint32_t k = 0; k < Ly.nk; ++k) mma_ts(slot + kWsAcc, slot + Ly.a_col + 8 * k, db + 2 * k, Ly.idesc, k);
+    for (uint32_t k = 0; k < Ly.nk; ++k) mma_ts<F8>(slot + kWsAcc, slot + Ly.a_col + 8 * k, db + 2 * k, Ly.idesc, k);
     if (Ly.nk2) {
       const uint64_t db2 = t5_desc(smem_u32(sW + Ly.b2_off));
-      for (uint32_t k = 0; k < Ly.nk2; ++k) mma_ts(slot + kWsAcc, slot + Ly.a2_col + 8 * k, db2 + 2 * k, Ly.idesc, 1u);
+      for (uint32_t k = 0; k < Ly.nk2; ++k)
+        mma_ts<F8>(slot + kWsAcc, slot + Ly.a2_col + 8 * k, db2 + 2 * k, Ly.idesc, 1u);
     }
     t5_commit(d_bar);
   }
@@ -237,6 +276,25 @@ __device__ __forceinline__ void ws_relu_layer(uint32_t my) {
   }
 }
 
+// Epilogue of a 64-wide hidden layer of the fp8 tier: row = e4m3(relu(m' acc + b')) with
+// m' = s_w s_a / s_a,next and b' = b / s_a,next (the next layer's input scale), 4 bytes a column.
+__device__ __forceinline__ void ws_relu_layer_f8(uint32_t my, float m, const float *__restrict__ b) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t v[32];
+    tm_ld32(my + kWsAcc + 32 * h, v);
+    uint32_t p[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = 32 * h + 4 * i;
+      p[i] = e4m3x4<true>(fmaf(__uint_as_float(v[4 * i]), m, b[c]), fmaf(__uint_as_float(v[4 * i + 1]), m, b[c + 1]),
+                          fmaf(__uint_as_float(v[4 * i + 2]), m, b[c + 2]),
+                          fmaf(__uint_as_float(v[4 * i + 3]), m, b[c + 3]));
+    }
+    tm_st8(my + kWsAct + 8 * h, p);
+  }
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, const uint8_t *__restrict__ wblob,
                                                                  const float4 *__restrict__ in, uint32_t n_fixed,
@@ -254,6 +312,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
   uint64_t *sBar = reinterpret_cast<uint64_t *>(sG + kPoseSmem);         // input ready[G], done[G], drain[G]
   WsLayer *sLay = reinterpret_cast<WsLayer *>(sBar + 3 * kWsGroups);
   uint32_t *sTmem = reinterpret_cast<uint32_t *>(sLay + kWsMaxLayers);
+  float *sF8 = reinterpret_cast<float *>(sTmem + 4);   // fp8 tier: m' per layer, then b' [layer][64]
+  constexpr bool F8 = kIsF8<T>;
 
   {  // a block with no tile leaves before any set-up (the live count is known only here)
     const uint32_t n0 = n_dev ? *n_dev : n_fixed;
@@ -283,7 +343,32 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
     __syncthreads();
     // biases into the B operands: columns 39 and 40 of residual layers 1 (the pose-folded bias)
     // and 4 (its gamma part), columns 0 and 1 of the bias tiles
-    if (tid < kWidth) {
+    if constexpr (F8) {
+      // fp8: per layer m' = m / s_a,next and b' = b / s_a,next for the epilogue (no bias in the
+      // products: e4m3 would keep 3 bits of it)
+      const int nl = (res ? 5 : 0) + H + 1, c0l = res ? 5 : 0;
+      const float *sc = P.fp8_scales;
+      auto bias_of = [&](int li, int n) -> float {
+        if (li < c0l) {
+          if (li == 0) return P.bias1[n];
+          if (li == 4) return n < 3 ? P.blob[P.lay.r5b + n] : 0.f;
+          return P.blob[(li == 1 ? P.lay.r2b : li == 2 ? P.lay.r3b : P.lay.r4b) + n];
+        }
+        const int c = li - c0l;
+        if (c == 0) return P.blob[P.lay.c0b + n];
+        if (c == H) return n < 4 ? P.blob[P.lay.clb + n] : 0.f;
+        return P.blob[P.lay.chb[c - 1] + n];
+      };
+      for (int i = tid; i < nl * kWidth; i += blockDim.x) {
+        const int li = i / kWidth, n = i % kWidth;
+        sF8[kWsMaxLayers + i] = bias_of(li, n) * sc[kF8SlotWs + 2 * li + 1];
+      }
+      if (tid < nl) sF8[tid] = sc[kF8SlotWs + 2 * tid] * sc[kF8SlotWs + 2 * tid + 1];
+      if (tid == 0) {   // 1 / s_a of gamma and of the hash encoding (the inputs the workers quantise)
+        sF8[kWsF8Inv] = sc[kF8SlotInvGam];
+        sF8[kWsF8Inv + 1] = sc[kF8SlotInvEnc];
+      }
+    } else if (tid < kWidth) {
       const int n = tid;
       // b = hi + lo, both rounded to the operand type, in columns k and k + 1
       auto put = [&](int tile, int k, float v) {
@@ -306,16 +391,29 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       auto add = [&](uint32_t a, int b, int nk, uint32_t a2, int b2, int nk2, int nout) {
         sLay[k++] = WsLayer{a, (uint32_t)b, (uint32_t)nk, a2, (uint32_t)b2, (uint32_t)nk2, t5_idesc(nout, fmt), 0u};
       };
-      if (res) {
-        add(kWsGam, L.r1, 3, 0, 0, 0, 64);
-        add(kWsAct, L.r2, 4, kWsOne, bt0 + 0 * kWsBiasTile, 1, 64);
-        add(kWsAct, L.r3, 4, kWsOne, bt0 + 1 * kWsBiasTile, 1, 64);
-        add(kWsAct, L.r4h, 4, kWsGam, L.r4g, 3, 64);
-        add(kWsAct, L.r5, 4, 0, 0, 0, 16);
+      if constexpr (F8) {   // K = 32 e4m3 values a step; gamma padded to 64
+        if (res) {
+          add(kWsGam, L.r1, 2, 0, 0, 0, 64);
+          add(kWsAct, L.r2, 2, 0, 0, 0, 64);
+          add(kWsAct, L.r3, 2, 0, 0, 0, 64);
+          add(kWsAct, L.r4h, 2, kWsGam, L.r4g, 2, 64);
+          add(kWsAct, L.r5, 2, 0, 0, 0, 16);
+        }
+        add(kWsAct, L.c0, 1, 0, 0, 0, 64);
+        for (int l = 0; l < H - 1; ++l) add(kWsAct, L.ch[l], 2, 0, 0, 0, 64);
+        add(kWsAct, L.cl, 2, 0, 0, 0, 16);
+      } else {
+        if (res) {
+          add(kWsGam, L.r1, 3, 0, 0, 0, 64);
+          add(kWsAct, L.r2, 4, kWsOne, bt0 + 0 * kWsBiasTile, 1, 64);
+          add(kWsAct, L.r3, 4, kWsOne, bt0 + 1 * kWsBiasTile, 1, 64);
+          add(kWsAct, L.r4h, 4, kWsGam, L.r4g, 3, 64);
+          add(kWsAct, L.r5, 4, 0, 0, 0, 16);
+        }
+        add(kWsAct, L.c0, kMlpIn / 16, kWsOne, bt0 + 2 * kWsBiasTile, 1, 64);
+        for (int l = 0; l < H - 1; ++l) add(kWsAct, L.ch[l], 4, kWsOne, bt0 + (3 + l) * kWsBiasTile, 1, 64);
+        add(kWsAct, L.cl, 4, 0, 0, 0, 16);
       }
-      add(kWsAct, L.c0, kMlpIn / 16, kWsOne, bt0 + 2 * kWsBiasTile, 1, 64);
-      for (int l = 0; l < H - 1; ++l) add(kWsAct, L.ch[l], 4, kWsOne, bt0 + (3 + l) * kWsBiasTile, 1, 64);
-      add(kWsAct, L.cl, 4, 0, 0, 0, 16);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -342,7 +440,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       const uint32_t t0 = blockIdx.x * kWsGroups + g;
       const uint32_t tiles = t0 < n_tiles ? (n_tiles - t0 + tstride - 1) / tstride : 0u;
       const int n_layers = (res ? 5 : 0) + H + 1;
-      ws_issue(tmem0 + (uint32_t)g * kWsSlotCols, smem_u32(sBar + g), smem_u32(sBar + kWsGroups + g),
+      ws_issue<F8>(tmem0 + (uint32_t)g * kWsSlotCols, smem_u32(sBar + g), smem_u32(sBar + kWsGroups + g),
                smem_u32(sBar + 2 * kWsGroups + g), sLay, n_layers, tiles * (uint32_t)n_layers, sW, err);
     }
     __syncwarp();
@@ -356,7 +454,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
     const uint32_t my = tmem0 + (uint32_t)g * kWsSlotCols + ((uint32_t)(q * 32) << 16);   // this warp's lanes
     uint32_t phase = 0;
     bool ok = true;
-    {  // the constant input block (1, 1, 0, ..., 0) of this thread's row; no layer writes it
+    if constexpr (!F8) {  // the constant input block (1, 1, 0, ..., 0) of this thread's row; no layer writes it
       const uint32_t c[8] = {pack2<T>(1.f, 1.f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
       tm_st8(my + kWsOne, c);
     }
@@ -436,17 +534,30 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
             sa = na; sb = nb; sd = nd;
           }
         }
-        gm[39] = 1.f;                                       // against the weights' bias columns
-        gm[40] = 1.f;
 #pragma unroll
         for (int k = 41; k < 48; ++k) gm[k] = 0.f;
-        uint32_t pa[16], pb[8];
+        if constexpr (F8) {   // 64 e4m3 values (39 used) in 16 columns, scaled by 1 / s_a
+          const float inv_gam = sF8[kWsF8Inv];
+          gm[39] = gm[40] = 0.f;
+          uint32_t pa[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) pa[k] = pack2<T>(gm[2 * k], gm[2 * k + 1]);
+          for (int k = 0; k < 12; ++k)
+            pa[k] = e4m3x4<false>(gm[4 * k] * inv_gam, gm[4 * k + 1] * inv_gam, gm[4 * k + 2] * inv_gam,
+                                  gm[4 * k + 3] * inv_gam);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) pb[k] = pack2<T>(gm[32 + 2 * k], gm[32 + 2 * k + 1]);
-        tm_st16(my + kWsGam, pa);
-        tm_st8(my + kWsGam + 16, pb);
+          for (int k = 12; k < 16; ++k) pa[k] = 0u;
+          tm_st16(my + kWsGam, pa);
+        } else {
+          gm[39] = 1.f;                                     // against the weights' bias columns
+          gm[40] = 1.f;
+          uint32_t pa[16], pb[8];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) pa[k] = pack2<T>(gm[2 * k], gm[2 * k + 1]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) pb[k] = pack2<T>(gm[32 + 2 * k], gm[32 + 2 * k + 1]);
+          tm_st16(my + kWsGam, pa);
+          tm_st8(my + kWsGam + 16, pb);
+        }
       }
       // the layers: residual 1 .. 5 (with MLP_res), then canonical 0 .. H; before canonical
       // layer 0 the hash encoding of x_final = x_skel + x_res fills the input columns
@@ -462,36 +573,81 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
           p0 = fminf(fmaxf(p0, 0.f), 1.f);
           p1 = fminf(fmaxf(p1, 0.f), 1.f);
           p2 = fminf(fmaxf(p2, 0.f), 1.f);
-          if (grouped_apply(P)) {
-            hash_encode_f16_grouped<T>(P, p0, p1, p2, inside,
-                                       [&](int l, uint32_t v) { tm_st1(my + kWsAct + (uint32_t)l, v); });
-          } else {
+          if constexpr (F8) {
+            // e4m3 pairs scaled by 1 / s_a, two levels to a column
+            const float inv_enc = sF8[kWsF8Inv + 1];
+            uint32_t pend = 0u;
+            auto emit8 = [&](int l, float fa, float fb) {
+              const uint32_t q = e4m3x4<false>(fa * inv_enc, fb * inv_enc, 0.f, 0.f) & 0xFFFFu;
+              if (l & 1)
+                tm_st1(my + kWsAct + (uint32_t)(l >> 1), pend | (q << 16));
+              else
+                pend = q;
+            };
+            if (grouped_apply(P)) {
+              hash_encode_f16_grouped<T>(P, p0, p1, p2, inside, [&](int l, uint32_t v) {
+                const float2 f = h2f2(v);
+                emit8(l, f.x, f.y);
+              });
+            } else {
 #pragma unroll 1
-            for (int l = 0; l < P.L; ++l) {
-              float fa, fb;
-              hash_level(P, l, p0, p1, p2, fa, fb);
-              tm_st1(my + kWsAct + (uint32_t)l, inside ? pack2<T>(fa, fb) : 0u);
+              for (int l = 0; l < P.L; ++l) {
+                float fa, fb;
+                hash_level(P, l, p0, p1, p2, fa, fb);
+                emit8(l, inside ? fa : 0.f, inside ? fb : 0.f);
+              }
             }
+            if (P.L & 1) tm_st1(my + kWsAct + (uint32_t)(P.L >> 1), pend);
+            for (int c = (P.L + 1) >> 1; c < kMaxLevels / 2; ++c) tm_st1(my + kWsAct + (uint32_t)c, 0u);
+          } else {
+            if (grouped_apply(P)) {
+              hash_encode_f16_grouped<T>(P, p0, p1, p2, inside,
+                                         [&](int l, uint32_t v) { tm_st1(my + kWsAct + (uint32_t)l, v); });
+            } else {
+#pragma unroll 1
+              for (int l = 0; l < P.L; ++l) {
+                float fa, fb;
+                hash_level(P, l, p0, p1, p2, fa, fb);
+                tm_st1(my + kWsAct + (uint32_t)l, inside ? pack2<T>(fa, fb) : 0u);
+              }
+            }
+            for (int l = P.L; l < kMaxLevels; ++l) tm_st1(my + kWsAct + (uint32_t)l, 0u);
           }
-          for (int l = P.L; l < kMaxLevels; ++l) tm_st1(my + kWsAct + (uint32_t)l, 0u);
         }
         ws_layer(G, phase, ok, err, overlap);
         if (li == n_layers - 1) break;
         if (res && li == 4) {                                 // residual layer 5: x_res
           float o3[4];
           tm_ld4(my + kWsAcc, o3);
-          f0 += o3[0] + sBias[bl.r5 + 0];
-          f1 += o3[1] + sBias[bl.r5 + 1];
-          f2 += o3[2] + sBias[bl.r5 + 2];
+          if constexpr (F8) {
+            const float *b8 = sF8 + kWsMaxLayers + 4 * kWidth;
+            f0 += fmaf(o3[0], sF8[4], b8[0]);
+            f1 += fmaf(o3[1], sF8[4], b8[1]);
+            f2 += fmaf(o3[2], sF8[4], b8[2]);
+          } else {
+            f0 += o3[0] + sBias[bl.r5 + 0];
+            f1 += o3[1] + sBias[bl.r5 + 1];
+            f2 += o3[2] + sBias[bl.r5 + 2];
+          }
+        } else if constexpr (F8) {
+          ws_relu_layer_f8(my, sF8[li], sF8 + kWsMaxLayers + li * kWidth);
         } else {
           ws_relu_layer<T>(my);
         }
       }
       float o[4];
       tm_ld4(my + kWsAcc, o);
+      if constexpr (F8) {
+        const int lo = n_layers - 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = fmaf(o[k], sF8[lo], sF8[kWsMaxLayers + lo * kWidth + k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] += sBias[bl.cl + k];
+      }
       if (valid) {
-        const float cr = sigmoidf_(o[0] + sBias[bl.cl]), cg = sigmoidf_(o[1] + sBias[bl.cl + 1]);
-        const float cb = sigmoidf_(o[2] + sBias[bl.cl + 2]), sigma = softplusf_(o[3] + sBias[bl.cl + 3]);
+        const float cr = sigmoidf_(o[0]), cg = sigmoidf_(o[1]);
+        const float cb = sigmoidf_(o[2]), sigma = softplusf_(o[3]);
         if (MODE == kModeRender) {
           const float al = inside ? -expm1f(-sigma * delta) * fminf(S, 1.f) : 0.f;
           reinterpret_cast<float4 *>(out)[j] = make_float4(cr, cg, cb, al);
@@ -518,6 +674,7 @@ static size_t ws_smem(int hidden) {
   size_t b = 1024 + (size_t)((L.total + 1023) & ~1023) + (size_t)(hidden + 2) * kWsBiasTile;
   b += sizeof(float) * (((bl.total + 3) & ~3) + kPoseSmem);
   b += sizeof(uint64_t) * (3 * kWsGroups) + sizeof(WsLayer) * kWsMaxLayers + 16;
+  b += sizeof(float) * (kWsF8Inv + 4);               // the fp8 tier's m', b' and input scales
   return b;
 }
 
@@ -533,7 +690,7 @@ static nr_status launch_ws_mode(const FieldParams &P, const uint8_t *blob, const
 
 nr_status launch_field_ws(const FieldParams &P, nr_dtype mlp_dtype, int mode, const float4 *in, uint32_t n_fixed,
                           const uint32_t *n_dev, float *out, int device, cudaStream_t st) {
-  if (!P.t5_bf16 || !P.t5_f16 || !P.t5_err) {
+  if (!P.t5_bf16 || !P.t5_f16 || !P.t5_err || (mlp_dtype == NR_FP8E4M3 && (!P.t5_fp8 || !P.fp8_scales))) {
     set_error("tcgen05 weights not prepared");
     return NR_ESTATE;
   }
@@ -541,6 +698,10 @@ nr_status launch_field_ws(const FieldParams &P, nr_dtype mlp_dtype, int mode, co
     set_error("tcgen05 pipeline: %d hidden layers (1..%d supported)", P.hidden, kMaxHidden);
     return NR_EUNSUPPORTED;
   }
+  if (mlp_dtype == NR_FP8E4M3)
+    return mode == kModeRender
+               ? launch_ws_mode<E4M3, kModeRender>(P, P.t5_fp8, in, n_fixed, n_dev, out, P.t5_err, device, st)
+               : launch_ws_mode<E4M3, kModeQuery>(P, P.t5_fp8, in, n_fixed, n_dev, out, P.t5_err, device, st);
   if (mlp_dtype == NR_BF16)
     return mode == kModeRender
                ? launch_ws_mode<__nv_bfloat16, kModeRender>(P, P.t5_bf16, in, n_fixed, n_dev, out, P.t5_err, device, st)

@@ -232,9 +232,11 @@ __device__ __forceinline__ uint32_t level_sum(const LevelCell &c, const uint32_t
   const uint32_t e = lerp_h2(v[4], v[5], fx), g = lerp_h2(v[6], v[7], fx);
   const uint32_t r = lerp_h2(lerp_h2(a, b, fy), lerp_h2(e, g, fy), fz);
   if (!inside) return 0u;
-  if (TcFmt<T>::value == 0) return r;
-  const float2 f = h2f2(r);
-  return pack2<T>(f.x, f.y);
+  if constexpr (TcFmt<T>::value == 0) return r;   // f16 operands (and the fp8 tier, which scales the pair)
+  else {
+    const float2 f = h2f2(r);
+    return pack2<T>(f.x, f.y);
+  }
 }
 
 // Levels l .. l + NL - 1 (each dense or hashed; the levels below n_dense are dense): every corner

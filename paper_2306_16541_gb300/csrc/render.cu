@@ -397,7 +397,9 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
       return launch_field_tc(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st, mma_path == 2 ? 2 : 1);
     return launch_field_ws(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
   }
-  if (mlp_dtype == NR_FP8E4M3) return launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st);
+  if (mlp_dtype == NR_FP8E4M3)
+    return mma_path == 4 ? launch_field_fp8(P, mode, in, n_fixed, n_dev, out, device, st)
+                         : launch_field_ws(P, mlp_dtype, mode, in, n_fixed, n_dev, out, device, st);
   if (mlp_dtype != NR_F32) {
     set_error("mlp_dtype %d is not implemented", (int)mlp_dtype);
     return NR_EUNSUPPORTED;
@@ -421,9 +423,11 @@ nr_status launch_field(const FieldParams &P, nr_dtype mlp_dtype, int mode, const
 // The field kernel a render or query takes (launch_field's mma_path): for bf16/f16 MLPs 0 the
 // warp-specialised tcgen05 pipeline (the default), 1 tcgen05 with one group per tile and the
 // activations through shared memory, 2 warp-level mma.sync over two m-tiles per weight read,
-// 4 warp-level mma.sync over one m-tile; for float32 3 the tensor-core tier, else CUDA cores.
+// 4 warp-level mma.sync over one m-tile; for fp8 0 the tcgen05 pipeline, 4 warp-level mma.sync;
+// for float32 3 the tensor-core tier, else CUDA cores.
 int render_path(const nr_render_opts *o) {
   if (o->mlp_dtype == NR_F32) return (o->flags & NR_RENDER_F32_TC) ? 3 : 0;
+  if (o->mlp_dtype == NR_FP8E4M3) return (o->flags & NR_RENDER_MMA_SYNC) ? 4 : 0;
   if (o->mlp_dtype != NR_BF16 && o->mlp_dtype != NR_F16) return 0;
   if (o->flags & NR_RENDER_TCGEN05) return 1;
   if (o->flags & NR_RENDER_MMA2) return 2;
@@ -433,6 +437,7 @@ int render_path(const nr_render_opts *o) {
 // Whether the path runs a tcgen05 kernel: it needs the swizzled weight blobs (prepare_t5) and
 // keeps an error word for bounded waits that gave up.
 bool path_uses_tcgen05(const nr_render_opts *o, int path) {
+  if (o->mlp_dtype == NR_FP8E4M3) return path == 0;
   return (o->mlp_dtype == NR_BF16 || o->mlp_dtype == NR_F16) && (path == 0 || path == 1);
 }
 

@@ -642,6 +642,7 @@ FieldParams field_params(const nr_subject *s, const nr_render_opts *o) {
   P.fp8_scales = s->fp8_scales;
   P.t5_bf16 = s->t5_bf16;
   P.t5_f16 = s->t5_f16;
+  P.t5_fp8 = s->t5_fp8;
   P.t5_err = s->t5_err;
   return P;
 }
@@ -669,7 +670,7 @@ static void free_subject(nr_subject *s) {
                   s->f_bias1, s->f_cam,  s->samp,     s->samp_out, s->ray_range, s->counter,   s->out_stage,
                   s->t_samp, s->t_out,   s->t_T,      s->t_raycnt, s->t_live,   s->t_scratch, s->t_wacc,    s->t_red,
                   s->loss_acc, s->f_dbias1, s->fp8_blob, s->fp8_scales, s->fp8_jobs, s->fp8_G,
-                  s->t5_bf16,  s->t5_f16,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
+                  s->t5_bf16,  s->t5_f16,  s->t5_fp8,  s->t5_err,  s->ray_state, s->ray_next, s->canon_bits, s->occ_raw,
                   s->ref, s->g_ref, s->ref_m, s->ref_v, s->f_root, s->f_dG, s->f_omega_o,
                   s->cnn, s->g_cnn, s->cnn_m, s->cnn_v, s->cnn_z, s->cnn_prior, s->cnn_act, s->cnn_grad,
                   s->bone_box, s->bone_ibox};
@@ -777,6 +778,7 @@ extern "C" nr_status nr_create_subject(const nr_subject_desc *d, void *stream, n
   ALLOC(s->tc_f16, (size_t)s->tlay.total * 2);
   ALLOC(s->t5_bf16, (size_t)t5_layout((int)s->hidden).total);   // tcgen05 weight blobs, packed on first use
   ALLOC(s->t5_f16, (size_t)t5_layout((int)s->hidden).total);
+  ALLOC(s->t5_fp8, (size_t)t5_layout((int)s->hidden).total);
   ALLOC(s->t5_err, sizeof(uint32_t));
   ALLOC(s->d_G, kBones * 12 * 4);
   ALLOC(s->d_omega, (2 * kBones * 3 + 3) * 4);

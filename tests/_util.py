@@ -18,7 +18,7 @@ def psnr(a, b, peak=1.0):
     return float("inf") if mse == 0 else 10 * np.log10(peak * peak / mse)
 
 
-def gpu_render(subj, pose, cam, occupancy, mlp="f32", feat="f32", t_min=0.0, host=False, matrices=None):
+def gpu_render(subj, pose, cam, occupancy, mlp="f32", feat="f32", t_min=0.0, host=False, matrices=None, **flags):
     nr = nrmod()
     S = nr.Subject(subj)
     try:
@@ -26,7 +26,7 @@ def gpu_render(subj, pose, cam, occupancy, mlp="f32", feat="f32", t_min=0.0, hos
             S.set_pose(matrices, matrices=True)
         else:
             S.set_pose(*pose)
-        opts = nr.make_opts(mlp, feat, occupancy, t_min)
+        opts = nr.make_opts(mlp, feat, occupancy, t_min, **flags)
         if host:
             out = np.zeros((cam.height, cam.width, 4), np.float32)
             S.render(cam, opts, out)

@@ -211,22 +211,27 @@ def test_tensor_core_query_matches_f32(tiny_structured):
 FP8_PSNR_DB = 50.0   # the reduced-precision bar; e4m3 keeps 3 mantissa bits (elements off by up to 1/16)
 
 
+@pytest.mark.parametrize("path", ["pipeline", "mma_sync"])
 @pytest.mark.parametrize("which", ["tiny_structured", "frame"])
-def test_fp8_tier_psnr(tiny_structured, frame, which):
+def test_fp8_tier_psnr(tiny_structured, frame, which, path):
     """FP8 E4M3 MLPs (per-matrix weight scales, calibrated static activation scales) against
-    the oracle; the measured PSNR is printed for the precision table."""
+    the oracle, on the tcgen05 pipeline (kind::f8f6f4, the default) and on mma.sync; the measured
+    PSNR is printed for the precision table."""
     if which == "frame":
         cfg, cam, occ = frame, _small(frame["camera"], 64), True
     else:
         cfg, cam, occ = tiny_structured, tiny_structured["camera"], False
-    got = gpu_render(cfg["subject"], cfg["pose"], cam, occ, mlp="fp8", feat="f16" if occ else "f32")
+    got = gpu_render(cfg["subject"], cfg["pose"], cam, occ, mlp="fp8", feat="f16" if occ else "f32",
+                     mma_sync=(path == "mma_sync"))
     ref = oracle_render(cfg["subject"], cfg["pose"], cam, occ).reshape(got.shape)
     p = psnr(got, ref)
-    print(f"fp8 {which}: PSNR {p:.2f} dB, max abs {np.abs(got - ref).max():.3e}")
+    print(f"fp8 {which} {path}: PSNR {p:.2f} dB, max abs {np.abs(got - ref).max():.3e}")
+    assert got[..., 3].max() > 0.1
     assert p >= FP8_PSNR_DB
 
 
-def test_fp8_is_batch_independent(tiny_structured):
+@pytest.mark.parametrize("path", ["pipeline", "mma_sync"])
+def test_fp8_is_batch_independent(tiny_structured, path):
     """Static scales: a point's fp8 result is the same whatever else is evaluated with it."""
     nr = nrmod()
     cfg = tiny_structured
@@ -234,8 +239,9 @@ def test_fp8_is_batch_independent(tiny_structured):
     S = nr.Subject(cfg["subject"])
     try:
         S.set_pose(*cfg["pose"])
-        full = S.query(x, nr.make_opts("fp8"))
-        part = S.query(x[:333].contiguous(), nr.make_opts("fp8"))
+        o = nr.make_opts("fp8", mma_sync=(path == "mma_sync"))
+        full = S.query(x, o)
+        part = S.query(x[:333].contiguous(), o)
         torch.cuda.synchronize()
         assert torch.equal(full[:333], part)
     finally:

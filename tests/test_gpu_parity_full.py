@@ -43,7 +43,7 @@ def frame_oracle():
 
 
 TIERS = [("f32", "f32", {}), ("f32", "f16", {}), ("bf16", "f16", {}), ("f16", "f16", {}),
-         ("bf16", "f16", {"mma_sync": True}), ("fp8", "f16", {})]
+         ("bf16", "f16", {"mma_sync": True}), ("fp8", "f16", {}), ("fp8", "f16", {"mma_sync": True})]
 
 
 @pytest.mark.parametrize("mlp,feat,path", TIERS, ids=[f"{m}-{f}-{'sync' if p else 'default'}" for m, f, p in TIERS])
