@@ -322,7 +322,7 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
     for n in sizes:
         outs.append(arena[off:off + 4 * n])
         off += 4 * n
-    srv = nr.Server(max_bytes=max_slots * (137 << 20), max_slots=max_slots, device=device)
+    srv = nr.Server(max_bytes=max_slots * (1200 << 20), max_slots=max_slots, device=device)   # 2^20-ray chunks
     if policy:
         srv.set_policy(**policy)
     for S in subs:

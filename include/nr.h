@@ -339,13 +339,16 @@ typedef struct {
   double rays_done;
 } nr_server_stats;
 
-/* Creates a server on `device` with a device-memory budget for its slots
- * (each slot needs about 136 MiB) and a slot limit (1..256); starts its
- * worker thread.  Queued requests are dispatched earliest deadline first
- * (nr_server_set_policy changes the order).  Few slots serve the latency
- * tail best (2 measured best at 240 req/s of the conferencing mix): every
- * field launch occupies all SMs, so requests running side by side stretch
- * one another.  NR_EINVAL if max_bytes cannot hold one slot. */
+/* Creates a server on `device` with a device-memory budget for its slots and a
+ * slot limit (1..256); starts its worker thread.  A slot renders a request in
+ * chunks of rays: the server takes the largest chunk from 2^17 rays (a slot of
+ * ~138 MB) to 2^20 rays (~1.10 GB, a 1024 x 1024 frame in one pass) for which
+ * max_slots slots fit max_bytes; fewer, larger passes cost less per frame.
+ * Queued requests are dispatched earliest deadline first (nr_server_set_policy
+ * changes the order).  Few slots serve the latency tail best (2 measured best
+ * at 240 req/s of the conferencing mix): every field launch occupies all SMs,
+ * so requests running side by side stretch one another.  NR_EINVAL if
+ * max_bytes cannot hold one slot of the smallest chunk. */
 nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t max_slots, nr_server **out);
 /* Dispatch policy of a server: the order in which queued requests are admitted
  * into free slots, and whether small requests run on high-priority streams. */
@@ -358,7 +361,7 @@ typedef struct {
   uint32_t order;                 /* NR_SERVE_* (default NR_SERVE_EDF) */
   float age_ms;                   /* smallest first: the aging bound (default 40) */
   float deadline_ms;              /* EDF: the deadline's constant part (default 20) */
-  float deadline_ms_per_mpixel;   /* EDF: its part per megapixel (default 20) */
+  float deadline_ms_per_mpixel;   /* EDF: its part per megapixel (default 5) */
   uint32_t priority_streams;      /* 1: requests of at most 512 x 512 pixels on high-priority
                                      streams, the rest on low-priority ones; 0: all alike (default) */
 } nr_server_policy;

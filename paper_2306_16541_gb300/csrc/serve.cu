@@ -10,13 +10,15 @@
 //   * one worker thread admits queued requests into slots in the order of the
 //     server's policy (nr_server_set_policy): earliest deadline first (deadline
 //     = arrival + deadline_ms + deadline_ms_per_mpixel x megapixels, 20 ms +
-//     20 ms per megapixel by default), smallest first (fewest pixel x sample
+//     5 ms per megapixel by default), smallest first (fewest pixel x sample
 //     slots; a request queued longer than age_ms goes first), or first come
 //     first served.  Few slots serve the tail best: each field launch holds
 //     every SM, so requests running side by side stretch each other.  A
 //     slot owns two CUDA streams (with priority streams on: high priority for
 //     requests of at most kSmallPixels pixels, low priority for the rest), the request's pose buffers (bone transforms,
-//     folded residual bias, posed occupancy bitfield) and its sample queues.
+//     folded residual bias, posed occupancy bitfield) and its sample queues,
+//     sized for the largest chunk of rays (2^17 .. 2^20) that max_slots slots
+//     fit in the budget.
 //     Slots are created on demand while the device-memory budget allows and are
 //     reused afterwards: admission is by memory and by slot count;
 //   * the worker enqueues the whole request on the slot's stream (pose upload,
@@ -42,8 +44,12 @@ namespace nr {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr size_t kSlotSamples = size_t(1) << 22;   // sample-queue entries per slot
-constexpr size_t kSlotRays = size_t(1) << 17;      // rays per chunk at most
+// A slot renders a request in chunks of at most its rays per chunk, with a sample queue of 32
+// entries per ray (one round of early termination at 128 samples per ray).  The server takes the
+// largest chunk in [kSlotRaysMin, kSlotRaysMax] for which max_slots slots fit its budget: a
+// 1024 x 1024 frame in one pass at 2^20 rays (~1.07 GB per slot), eight passes at 2^17 (~137 MB).
+constexpr size_t kSlotRaysMin = size_t(1) << 17, kSlotRaysMax = size_t(1) << 20;
+constexpr size_t kSlotSamplesPerRay = 32;
 constexpr double kAgeMs = 40.0;                      // a request queued this long is dispatched first
 constexpr uint64_t kSmallPixels = 512 * 512;         // requests up to this size run on high-priority streams
 
@@ -80,6 +86,7 @@ struct nr_server {
   int device = 0;
   uint64_t max_bytes = 0;
   uint32_t max_slots = 0;
+  size_t slot_rays = 0;               // rays per chunk of every slot of this server
   std::vector<nr_subject *> subjects;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -92,7 +99,7 @@ struct nr_server {
   bool stopping = false, worker_exit = false;
   std::thread worker;
   nr_server_stats st{};
-  nr_server_policy pol{NR_SERVE_EDF, (float)nr::kAgeMs, 20.f, 20.f, 0u};
+  nr_server_policy pol{NR_SERVE_EDF, (float)nr::kAgeMs, 20.f, 5.f, 0u};
 };
 
 namespace nr {
@@ -104,9 +111,9 @@ struct DoneCtx {
 
 static bool server_ok(const nr_server *s) { return s && s->magic == 0x4e525356u; }
 
-static size_t slot_bytes(int grid) {
-  return kSlotSamples * 2 * sizeof(float4) + kSlotRays * (sizeof(uint2) + sizeof(float4) + sizeof(uint32_t)) + 256 +
-         (size_t)grid * grid * grid / 8 + (kBones * 12 + kBones * 3 + kWidth) * sizeof(float);
+static size_t slot_bytes(int grid, size_t rays) {
+  return rays * kSlotSamplesPerRay * 2 * sizeof(float4) + rays * (sizeof(uint2) + sizeof(float4) + sizeof(uint32_t)) +
+         256 + (size_t)grid * grid * grid / 8 + (kBones * 12 + kBones * 3 + kWidth) * sizeof(float);
 }
 
 static void free_slot(Slot *sl) {
@@ -145,21 +152,22 @@ static nr_status make_slot(nr_server *srv, int grid, Slot **out) {
   SLOT_ALLOC(sl->d_omega, (2 * kBones * 3 + 3) * sizeof(float));
   SLOT_ALLOC(sl->d_bias1, kWidth * sizeof(float));
   SLOT_ALLOC(sl->bits, (size_t)grid * grid * grid / 8);
-  SLOT_ALLOC(sl->w.samp, kSlotSamples * sizeof(float4));
-  SLOT_ALLOC(sl->w.samp_out, kSlotSamples * sizeof(float4));
-  SLOT_ALLOC(sl->w.ray_range, kSlotRays * sizeof(uint2));
+  const size_t rays = srv->slot_rays, samples = rays * kSlotSamplesPerRay;
+  SLOT_ALLOC(sl->w.samp, samples * sizeof(float4));
+  SLOT_ALLOC(sl->w.samp_out, samples * sizeof(float4));
+  SLOT_ALLOC(sl->w.ray_range, rays * sizeof(uint2));
   SLOT_ALLOC(sl->w.counter, 256);
-  SLOT_ALLOC(sl->w.state, kSlotRays * sizeof(float4));
-  SLOT_ALLOC(sl->w.next, kSlotRays * sizeof(uint32_t));
+  SLOT_ALLOC(sl->w.state, rays * sizeof(float4));
+  SLOT_ALLOC(sl->w.next, rays * sizeof(uint32_t));
   SLOT_ALLOC(sl->d_err, sizeof(uint32_t));
 #undef SLOT_ALLOC
   if ((e = cudaMallocHost((void **)&sl->h_pose, (kBones * 12 + kBones * 3 + 3) * sizeof(float))) != cudaSuccess)
     return fail(e, "pinned pose buffer");
   if ((e = cudaMallocHost((void **)&sl->h_err, sizeof(uint32_t))) != cudaSuccess) return fail(e, "pinned error word");
   *sl->h_err = 0;
-  sl->w.cap_samples = kSlotSamples;
-  sl->w.cap_rays = kSlotRays;
-  sl->bytes = slot_bytes(grid);
+  sl->w.cap_samples = samples;
+  sl->w.cap_rays = rays;
+  sl->bytes = slot_bytes(grid, rays);
   sl->index = (int)srv->slots.size();
   *out = sl;
   return NR_OK;
@@ -243,7 +251,7 @@ static void worker_main(nr_server *srv) {
         }
       if (!slot && srv->slots.size() < srv->max_slots) {
         const int grid = srv->subjects.empty() ? 128 : (int)srv->subjects[0]->occ_grid;
-        if (srv->bytes_in_use + slot_bytes(grid) <= srv->max_bytes) {
+        if (srv->bytes_in_use + slot_bytes(grid, srv->slot_rays) <= srv->max_bytes) {
           Slot *ns = nullptr;
           if (make_slot(srv, grid, &ns) == NR_OK) {
             srv->slots.push_back(ns);
@@ -335,12 +343,17 @@ extern "C" nr_status nr_server_create(int device, uint64_t max_bytes, uint32_t m
   NR_REQUIRE(out, "nr_server_create: NULL out");
   *out = nullptr;
   NR_REQUIRE(max_slots >= 1 && max_slots <= 256, "nr_server_create: max_slots must be 1..256");
-  NR_REQUIRE(max_bytes >= slot_bytes(32), "nr_server_create: max_bytes below one slot (%zu bytes)", slot_bytes(32));
+  NR_REQUIRE(max_bytes >= slot_bytes(32, kSlotRaysMin), "nr_server_create: max_bytes below one slot (%zu bytes)",
+             slot_bytes(32, kSlotRaysMin));
   NR_CHECK_CUDA(cudaSetDevice(device));
   nr_server *srv = new nr_server();
   srv->device = device;
   srv->max_bytes = max_bytes;
   srv->max_slots = max_slots;
+  // the largest chunk for which max_slots slots (128^3 occupancy grids) fit the budget
+  srv->slot_rays = kSlotRaysMin;
+  while (srv->slot_rays < kSlotRaysMax && slot_bytes(128, 2 * srv->slot_rays) * max_slots <= max_bytes)
+    srv->slot_rays *= 2;
   srv->worker = std::thread(worker_main, srv);
   *out = srv;
   return NR_OK;

@@ -537,7 +537,7 @@ class Server:
         self.subjects = []
 
     def set_policy(self, order: int = NR_SERVE_EDF, age_ms: float = 40.0, deadline_ms: float = 20.0,
-                   deadline_ms_per_mpixel: float = 20.0, priority_streams: bool = False) -> None:
+                   deadline_ms_per_mpixel: float = 5.0, priority_streams: bool = False) -> None:
         p = nr_server_policy(int(order), float(age_ms), float(deadline_ms), float(deadline_ms_per_mpixel),
                              int(bool(priority_streams)))
         check(lib.nr_server_set_policy(self.h, C.byref(p)), "nr_server_set_policy")

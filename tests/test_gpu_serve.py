@@ -57,6 +57,7 @@ def test_mix_equals_alone(subjects, order):
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["failed"] == 0
         assert st["peak_active"] > 1                    # requests really overlapped on the device
+        assert st["bytes_in_use"] >= st["slots"] * (1 << 30)   # the budget allows 2^20-ray chunks
         assert all(l > 0 for l in lat)
         for q, out in zip(reqs, outs):
             S = subs[q["subject"]]
@@ -87,9 +88,35 @@ def test_admission_by_memory_budget_and_pinned_host_output(subjects):
             srv.wait(i, 60000)
         st = srv.stats()
         assert st["slots"] == 1 and st["peak_active"] == 1 and st["completed"] == 6
+        assert st["bytes_in_use"] <= one_slot               # 2^17-ray chunks: larger frames take several
         q = reqs[-1]
         S.set_pose(q["aa"], q["rt"])
         assert torch.equal(outs[-1], S.render(q["cam"], nr.make_opts("f32")).cpu())
+    finally:
+        srv.close()
+        S.close()
+
+
+def test_frames_larger_than_a_chunk_equal_the_plain_render(subjects):
+    """A 512 x 384 request (196,608 rays) on a server whose budget allows only 2^17-ray chunks is
+    rendered in two passes; the image equals nr_render's single pass bit for bit."""
+    nr = nrmod()
+    S = nr.Subject(subjects[2])
+    srv = nr.Server(max_bytes=137 << 20, max_slots=1)
+    try:
+        srv.add_subject(S)
+        rng = np.random.default_rng(77)
+        cam = synth.camera(512, 384, 480.0, synth.random_eye(rng), 32, 0.5, 4.5)
+        aa, rt = synth.random_pose(rng)
+        for mlp in ("f32", "bf16"):
+            opts = nr.make_opts(mlp, "f32", True, 1e-4)
+            out = torch.full((384, 512, 4), float("nan"), device="cuda")
+            srv.wait(srv.submit(srv.request(0, cam, aa, rt, opts, out)), 60000)
+            S.set_pose(aa, rt)
+            alone = S.render(cam, opts)
+            torch.cuda.synchronize()
+            assert torch.equal(out, alone), mlp
+        assert srv.stats()["bytes_in_use"] <= 137 << 20
     finally:
         srv.close()
         S.close()

@@ -84,8 +84,9 @@ def _rel(a, b):
 # Relative L2 bounds per group.  The weight volume's bound is looser: a sample
 # whose bone-weight sum S lies under the 1e-4 floor moves its canonical point
 # by p_i / 1e-4 per unit weight, so a float32-vs-float64 ReLU or cell-face flip
-# at such a sample shifts many voxel gradients at once (see _smooth).
-TOL = {"wvol": 1e-2, "table": 1e-3, "mlp": 1e-3, "res": 1e-3}
+# at such a sample shifts many voxel gradients at once (see _smooth).  Measured
+# on this batch: 4.5e-3 (the other groups 4e-7 .. 6e-5).
+TOL = {"wvol": 6e-3, "table": 1e-3, "mlp": 1e-3, "res": 1e-3}
 
 
 def test_gradients_match_oracle():
@@ -93,6 +94,7 @@ def test_gradients_match_oracle():
     loss, grads, _, _ = _gpu_step(subj, frames, batch, tgt, 16, 77, grad_only=True)
     ref_loss, ref = _oracle_grads(subj, frames, batch, tgt, 16, 77)
     assert abs(loss - ref_loss) <= 1e-5 * max(1.0, ref_loss), (loss, ref_loss)
+    print("relative L2 per group:", {g: _rel(grads[g], ref[g]) for g in GROUPS})
     for g in GROUPS:
         assert np.linalg.norm(ref[g]) > 0, g
         assert _rel(grads[g], ref[g]) <= TOL[g], (g, _rel(grads[g], ref[g]))
