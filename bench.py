@@ -333,13 +333,20 @@ def serve_bench(nr, device, mlp, rate=240.0, duration=3.0, n_subjects=8, max_slo
     for w in warm:
         srv.wait(w, 120000)
     torch.cuda.synchronize()
+    # the request records are built before the clock starts; each is submitted at its arrival
+    # time (a sleep to within 1 ms of it, then a spin: a plain sleep wakes late and bunches arrivals)
+    built = [srv.request(q["subject"], q["camera"], q["axis_angle"], q["root_t"], opts, outs[i])
+             for i, q in enumerate(reqs)]
     t0 = time.perf_counter()
     ids = []
-    for i, q in enumerate(reqs):
-        dt = t0 + q["t_arrive"] - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        ids.append(srv.submit(srv.request(q["subject"], q["camera"], q["axis_angle"], q["root_t"], opts, outs[i])))
+    for q, rq in zip(reqs, built):
+        due = t0 + q["t_arrive"]
+        dt = due - time.perf_counter()
+        if dt > 1e-3:
+            time.sleep(dt - 1e-3)
+        while time.perf_counter() < due:
+            pass
+        ids.append(srv.submit(rq))
     lat = [srv.wait(i, 600000) for i in ids]
     t_end = time.perf_counter()
     st = srv.stats()

@@ -164,3 +164,15 @@ def test_server_policy_refused_without_a_server(nr):
     pol = nr.nr_server_policy(nr.NR_SERVE_EDF, 40.0, 20.0, 20.0, 0)
     assert nr.lib.nr_server_set_policy(None, C.byref(pol)) == nr.NR_EINVAL
     assert b"nr_server_set_policy" in nr.lib.nr_last_error()
+
+
+def test_gather_rate_arguments_checked_without_gpu(nr):
+    """nr_l2_gather_rate refuses a NULL output, load sizes other than 4 or 16 bytes and tables
+    that are not a power of two in [1 MiB, 1 GiB] before it touches a device."""
+    v = C.c_double()
+    assert nr.lib.nr_l2_gather_rate(0, 32 << 20, 4, None) == nr.NR_EINVAL
+    assert nr.lib.nr_l2_gather_rate(0, 32 << 20, 8, C.byref(v)) == nr.NR_EINVAL
+    assert b"load_bytes" in nr.lib.nr_last_error()
+    assert nr.lib.nr_l2_gather_rate(0, (32 << 20) + 4096, 4, C.byref(v)) == nr.NR_EINVAL
+    assert nr.lib.nr_l2_gather_rate(0, 1 << 19, 16, C.byref(v)) == nr.NR_EINVAL
+    assert b"table_bytes" in nr.lib.nr_last_error()
