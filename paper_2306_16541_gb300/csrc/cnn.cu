@@ -46,40 +46,50 @@ __global__ void cnn_fc_fwd(const float *__restrict__ W, const float *__restrict_
   h[o] = leaky(a);
 }
 
-// out[o][u] = b[o] + sum_i sum_taps in[i][tap] W[i][o][k(tap)], one thread per output
+// out[o][u] = b[o] + sum_i sum_taps in[i][tap] W[i][o][k(tap)]: `split` consecutive lanes per
+// output (a power of two up to 32), lane j taking inputs i = j, j + split, ... and the group
+// summing over shuffles, so that the first layers' few outputs still fill the GPU
 __global__ void __launch_bounds__(256) cnn_convt_fwd(const float *__restrict__ in, const float *__restrict__ W,
                                                      const float *__restrict__ b, int Cin, int Cout, int r,
-                                                     int act, float *__restrict__ out) {
+                                                     int act, int split, float *__restrict__ out) {
   const int R = 2 * r;
   const size_t n = (size_t)Cout * R * R * R;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  const int x = (int)(idx % R), y = (int)((idx / R) % R), zz = (int)((idx / ((size_t)R * R)) % R);
-  const int o = (int)(idx / ((size_t)R * R * R));
-  int iz[2], kz[2], iy[2], ky[2], ix[2], kx[2];
-  taps(zz, r, iz, kz);
-  taps(y, r, iy, ky);
-  taps(x, r, ix, kx);
-  const size_t r3 = (size_t)r * r * r;
-  float acc = b[o];
-  for (int i = 0; i < Cin; ++i) {
-    const float *wi = W + ((size_t)i * Cout + o) * 64;
-    const float *xi = in + (size_t)i * r3;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t idx = t / split;
+  const int j = (int)(t % split);
+  const bool valid = idx < n;
+  float acc = 0.f;
+  if (valid) {
+    const int x = (int)(idx % R), y = (int)((idx / R) % R), zz = (int)((idx / ((size_t)R * R)) % R);
+    const int o = (int)(idx / ((size_t)R * R * R));
+    int iz[2], kz[2], iy[2], ky[2], ix[2], kx[2];
+    taps(zz, r, iz, kz);
+    taps(y, r, iy, ky);
+    taps(x, r, ix, kx);
+    const size_t r3 = (size_t)r * r * r;
+    for (int i = j; i < Cin; i += split) {
+      const float *wi = W + ((size_t)i * Cout + o) * 64;
+      const float *xi = in + (size_t)i * r3;
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      if (iz[a] < 0) continue;
+      for (int a = 0; a < 2; ++a) {
+        if (iz[a] < 0) continue;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        if (iy[c] < 0) continue;
+        for (int c = 0; c < 2; ++c) {
+          if (iy[c] < 0) continue;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          if (ix[e] < 0) continue;
-          acc = fmaf(xi[((size_t)iz[a] * r + iy[c]) * r + ix[e]], wi[(kz[a] * 4 + ky[c]) * 4 + kx[e]], acc);
+          for (int e = 0; e < 2; ++e) {
+            if (ix[e] < 0) continue;
+            acc = fmaf(xi[((size_t)iz[a] * r + iy[c]) * r + ix[e]], wi[(kz[a] * 4 + ky[c]) * 4 + kx[e]], acc);
+          }
         }
       }
     }
   }
-  out[idx] = act ? leaky(acc) : acc;
+  for (int off = split >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (valid && j == 0) {
+    acc += b[idx / ((size_t)R * R * R)];
+    out[idx] = act ? leaky(acc) : acc;
+  }
 }
 
 // W^c[c][v] = softmax_c(logit[c][v] + log_prior[c][v])
@@ -119,37 +129,43 @@ __global__ void cnn_softmax_bwd(const float *__restrict__ w, const float *__rest
   }
 }
 
-// din[i][q] = leaky'(in[i][q]) sum_o sum_k W[i][o][k] dout[o][2 q - 1 + k], one thread per input
+// din[i][q] = leaky'(in[i][q]) sum_o sum_k W[i][o][k] dout[o][2 q - 1 + k]: `split` lanes per
+// input (outputs o = j, j + split, ...), summed over shuffles
 __global__ void __launch_bounds__(256) cnn_convt_bwd_data(const float *__restrict__ in, const float *__restrict__ W,
                                                           const float *__restrict__ dout, int Cin, int Cout, int r,
-                                                          float *__restrict__ din) {
+                                                          int split, float *__restrict__ din) {
   const size_t r3 = (size_t)r * r * r;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)Cin * r3) return;
-  const int q = (int)(idx % r3), i = (int)(idx / r3);
-  const int x = q % r, y = (q / r) % r, zz = q / (r * r);
-  const int R = 2 * r;
-  const size_t R3 = (size_t)R * R * R;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t idx = t / split;
+  const int j = (int)(t % split);
+  const bool valid = idx < (size_t)Cin * r3;
   float acc = 0.f;
-  for (int o = 0; o < Cout; ++o) {
-    const float *wi = W + ((size_t)i * Cout + o) * 64;
-    const float *go = dout + (size_t)o * R3;
-    for (int kz = 0; kz < 4; ++kz) {
-      const int uz = 2 * zz - 1 + kz;
-      if (uz < 0 || uz >= R) continue;
-      for (int ky = 0; ky < 4; ++ky) {
-        const int uy = 2 * y - 1 + ky;
-        if (uy < 0 || uy >= R) continue;
+  if (valid) {
+    const int q = (int)(idx % r3), i = (int)(idx / r3);
+    const int x = q % r, y = (q / r) % r, zz = q / (r * r);
+    const int R = 2 * r;
+    const size_t R3 = (size_t)R * R * R;
+    for (int o = j; o < Cout; o += split) {
+      const float *wi = W + ((size_t)i * Cout + o) * 64;
+      const float *go = dout + (size_t)o * R3;
+      for (int kz = 0; kz < 4; ++kz) {
+        const int uz = 2 * zz - 1 + kz;
+        if (uz < 0 || uz >= R) continue;
+        for (int ky = 0; ky < 4; ++ky) {
+          const int uy = 2 * y - 1 + ky;
+          if (uy < 0 || uy >= R) continue;
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-          const int ux = 2 * x - 1 + kx;
-          if (ux < 0 || ux >= R) continue;
-          acc = fmaf(wi[(kz * 4 + ky) * 4 + kx], go[((size_t)uz * R + uy) * R + ux], acc);
+          for (int kx = 0; kx < 4; ++kx) {
+            const int ux = 2 * x - 1 + kx;
+            if (ux < 0 || ux >= R) continue;
+            acc = fmaf(wi[(kz * 4 + ky) * 4 + kx], go[((size_t)uz * R + uy) * R + ux], acc);
+          }
         }
       }
     }
   }
-  din[idx] = acc * leaky_grad(in[idx]);
+  for (int off = split >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (valid && j == 0) din[idx] = acc * leaky_grad(in[idx]);
 }
 
 // dW[i][o][k] = sum_q in[i][q] dout[o][2 q - 1 + k], one thread per weight (k fastest)
@@ -251,6 +267,14 @@ static CnnLayout cnn_layout(const uint32_t *ch) {
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
 
+// Lanes per output of a layer with n outputs, each a sum over `terms` inputs (or outputs): enough
+// that the launch reaches ~2^18 threads, at most 32 and no more than the terms.
+static int cnn_split(size_t n, int terms) {
+  int sp = 1;
+  while (sp < 32 && sp < terms && n * (size_t)sp < (size_t(1) << 18)) sp *= 2;
+  return sp;
+}
+
 // W^c = CNN_skel(z) into s->wvol; keeps the activations for the backward.
 nr_status cnn_forward(nr_subject *s, cudaStream_t st) {
   const CnnLayout L = cnn_layout(s->cnn_ch);
@@ -259,9 +283,11 @@ nr_status cnn_forward(nr_subject *s, cudaStream_t st) {
                                                      A + L.act[0]);
   for (int k = 1; k <= 5; ++k) {
     const size_t R = 2 * (size_t)L.r[k];
-    cnn_convt_fwd<<<blocks_for((size_t)L.cout[k] * R * R * R), 256, 0, st>>>(
-        A + L.act[k - 1], s->cnn + L.w[k], s->cnn + L.b[k], L.cin[k], L.cout[k], L.r[k], k < 5 ? 1 : 0,
-        A + L.act[k]);
+    const size_t nout = (size_t)L.cout[k] * R * R * R;
+    const int sp = cnn_split(nout, L.cin[k]);
+    cnn_convt_fwd<<<blocks_for(nout * sp), 256, 0, st>>>(A + L.act[k - 1], s->cnn + L.w[k], s->cnn + L.b[k],
+                                                         L.cin[k], L.cout[k], L.r[k], k < 5 ? 1 : 0, sp,
+                                                         A + L.act[k]);
   }
   const int V = kCnnRes * kCnnRes * kCnnRes;
   cnn_softmax_fwd<<<blocks_for(V), 256, 0, st>>>(A + L.act[5], s->cnn_prior, V, s->wvol);
@@ -286,8 +312,9 @@ nr_status cnn_backward(nr_subject *s, cudaStream_t st) {
         A + L.act[k - 1], d0, L.cin[k], L.cout[k], L.r[k], s->g_cnn + L.w[k]);
     cnn_bias_grad<<<L.cout[k], 256, 0, st>>>(d0, (int)nout, s->g_cnn + L.b[k]);
     const size_t nin = (size_t)L.cin[k] * L.r[k] * L.r[k] * L.r[k];
-    cnn_convt_bwd_data<<<blocks_for(nin), 256, 0, st>>>(A + L.act[k - 1], s->cnn + L.w[k], d0, L.cin[k],
-                                                        L.cout[k], L.r[k], d1);
+    const int sp = cnn_split(nin, L.cout[k]);
+    cnn_convt_bwd_data<<<blocks_for(nin * sp), 256, 0, st>>>(A + L.act[k - 1], s->cnn + L.w[k], d0, L.cin[k],
+                                                             L.cout[k], L.r[k], sp, d1);
     std::swap(d0, d1);
     launched += 3;
   }
