@@ -516,12 +516,78 @@ __global__ void __launch_bounds__(kFwdThreads, 1) train_fwd_kernel(FieldParams P
   }
 }
 
+// The compositing adjoint of train_composite_kernel for the RB rays whose slots a block holds
+// (ray slots rs0 .. rs0 + RB - 1; local ray lr's samples at o[lr S ..]), by the block's first
+// warp: o[] holds each slot's (r, g, b, alpha) on entry and its (dL/dc, dL/dalpha) on exit,
+// Ts[] the transmittance in front of each sample.  Same arithmetic in the same order.
+__device__ __forceinline__ void composite_rays(const TrainDev &T, float4 *o, float *Ts, uint32_t rs0, uint32_t RB) {
+  const int lane = threadIdx.x & 31;
+  float lsum = 0.f;
+  for (uint32_t lr = lane; lr < RB; lr += 32) {
+    const uint32_t rs = rs0 + lr;
+    if (rs >= T.n_rays) break;
+    const uint32_t r = (uint32_t)(((uint64_t)rs * T.ray_mul) % T.n_rays);
+    float4 *v4 = o + (size_t)lr * T.S;
+    float *t4 = Ts + (size_t)lr * T.S;
+    const uint32_t cnt = T.raycnt[r];
+    float Tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    for (uint32_t i = 0; i < cnt; ++i) {
+      const float4 v = v4[i];
+      t4[i] = Tr;
+      const float w = Tr * v.w;
+      c0 = fmaf(w, v.x, c0);
+      c1 = fmaf(w, v.y, c1);
+      c2 = fmaf(w, v.z, c2);
+      Tr *= 1.f - v.w;
+    }
+    const float C0 = fmaf(Tr, T.bg[0], c0), C1 = fmaf(Tr, T.bg[1], c1), C2 = fmaf(Tr, T.bg[2], c2);
+    if (T.pred) {
+      T.pred[3 * r] = C0;
+      T.pred[3 * r + 1] = C1;
+      T.pred[3 * r + 2] = C2;
+    }
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (T.grad_rgb) {
+      g0 = T.grad_rgb[3 * r];
+      g1 = T.grad_rgb[3 * r + 1];
+      g2 = T.grad_rgb[3 * r + 2];
+    } else if (T.target) {
+      const float e0 = C0 - T.target[3 * r], e1 = C1 - T.target[3 * r + 1], e2 = C2 - T.target[3 * r + 2];
+      lsum += T.loss_weight * (e0 * e0 + e1 * e1 + e2 * e2);
+      const float scale = 2.f * T.loss_weight / (3.f * (float)T.n_rays);
+      g0 = scale * e0;
+      g1 = scale * e1;
+      g2 = scale * e2;
+    }
+    float B = T.bg[0] * g0 + T.bg[1] * g1 + T.bg[2] * g2;
+    for (int i = (int)cnt - 1; i >= 0; --i) {
+      const float4 v = v4[i];
+      const float Ti = t4[i];
+      const float cg = v.x * g0 + v.y * g1 + v.z * g2;
+      const float ta = Ti * v.w;
+      v4[i] = make_float4(ta * g0, ta * g1, ta * g2, Ti * (cg - B));
+      B = fmaf(v.w, cg, (1.f - v.w) * B);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+  if (lane == 0 && lsum != 0.f) atomicAdd(T.loss, lsum / (3.f * (float)T.n_rays));
+}
+
 // One thread per sample: forward recompute (activations into the thread's scratch
 // column), backward, scatter-adds, then the warp's weight-gradient reduction.
+// FUSED: the forward and the compositing adjoint run here too, so that neither train_fwd_kernel
+// nor train_composite_kernel is needed: the block takes groups of whole rays (RB = blockDim / S
+// of them), evaluates every sample once, composites its rays in shared memory and goes straight
+// on to the backward with the activations still in its columns.
+template <bool FUSED>
 __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P, TrainDev T) {
   extern __shared__ float4 smem4[];
   float *sW = reinterpret_cast<float *>(smem4);        // the weights in the padded layout T.pl
   float *sdG = sW + T.pl.total;                        // [F][24][12] when T.dG_smem
+  // FUSED: each slot's (r, g, b, alpha), then its adjoint [SB], and transmittances [SB]
+  float4 *sOut = reinterpret_cast<float4 *>(sdG + (T.dG && T.dG_smem ? T.n_frames * kBones * 12 : 0));
+  float *sT = reinterpret_cast<float *>(sOut + blockDim.x);
   for (int q = 0; q < T.pl.n_seg; ++q) {
     const PadSeg &sg = T.pl.seg[q];
     for (int i = threadIdx.x; i < sg.rows * sg.cols; i += blockDim.x) {
@@ -547,23 +613,34 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
   const int H = P.hidden;
   const uint32_t n = T.n_rays * T.S;
   const uint32_t step = gridDim.x * blockDim.x;
-  const uint32_t n_iter = (n + step - 1) / step;
-  for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t q = it * step + blockIdx.x * blockDim.x + threadIdx.x;   // thread slot
-    const uint32_t r = q < n ? ray_of(T, q) : 0;
+  const uint32_t RB = FUSED ? blockDim.x / T.S : 0u, SB = RB * T.S;   // FUSED: rays and slots a group
+  const uint32_t n_units = FUSED ? (T.n_rays + RB - 1) / RB : (n + step - 1) / step;
+  for (uint32_t it = FUSED ? blockIdx.x : 0u; it < n_units; it += FUSED ? gridDim.x : 1u) {
+    const uint32_t q = FUSED ? it * SB + threadIdx.x : it * step + blockIdx.x * blockDim.x + threadIdx.x;  // slot
+    const bool qv = q < n && (!FUSED || threadIdx.x < SB);
+    const uint32_t q0 = q - lane;                                               // the warp's first slot
+    const uint32_t r = qv ? ray_of(T, q) : 0;
     const uint32_t j = r * T.S + q % T.S;                                       // sample slot
-    // the forward's mask: a slot outside it (no box hit, or warped out of the canonical box)
-    // adds exactly zero to every gradient, and a warp without live slots has nothing to do
-    const uint32_t lw = q - lane < n ? T.live[(q - lane) >> 5] : 0u;
-    if (lw == 0u) continue;
-    bool active = (lw >> lane) & 1u;
+    bool active;
+    if constexpr (FUSED) {
+      active = qv && T.raycnt[r] != 0;   // every slot of a ray that meets the box is evaluated
+    } else {
+      // the forward's mask: a slot outside it (no box hit, or warped out of the canonical box)
+      // adds exactly zero to every gradient, and a warp without live slots has nothing to do
+      const uint32_t lw = q0 < n ? T.live[q0 >> 5] : 0u;
+      if (lw == 0u) continue;
+      active = (lw >> lane) & 1u;
+    }
     const uint32_t f = active ? T.frame_id[r] : 0;
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active) g4 = __ldcs(T.out + j);
+    if (!FUSED && active) g4 = __ldcs(T.out + j);
+    const bool run = !FUSED || __any_sync(0xffffffffu, active);   // warp-uniform
     // per-sample state carried across the warp-level phases below
     const float *G = T.fG + (size_t)f * kBones * 12;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     float xs0 = 0.f, xs1 = 0.f, xs2 = 0.f, S = 0.f, xf0 = 0.f, xf1 = 0.f, xf2 = 0.f, dS_alpha = 0.f;
+    bool inside = false;
+    if (run) {
     // ---------------- forward recompute: per-sample gathers, warp-level MLP layers
     if (active) {
       s = __ldcs(T.samp + j);
@@ -588,7 +665,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       // x_res into the (not yet used) rows of the residual output's delta
       warp_fwd<4, kWidth, 0>(sW + PL.r5, 4, wcol, stride, R_RH + 3 * kWidth, 0, sW + PL.r5b, nullptr, 0, false, D_R5);
     }
-    bool inside = false;
     if (active) {
       if (P.res_enabled) {
         xf0 += col[(D_R5 + 0) * stride];
@@ -609,6 +685,24 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     // the canonical output o into the rows of its delta, read back by each sample's thread
     warp_fwd<4, kWidth, 0>(sW + PL.cl, 4, wcol, stride, R_CH + (H - 1) * kWidth, 0, sW + PL.clb, nullptr, 0, false,
                            D_CL);
+    }
+    if constexpr (FUSED) {
+      // each slot's (r, g, b, alpha) as train_fwd_kernel forms it, the rays composited in shared
+      // memory by the first warp, and each slot's adjoint back
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) {
+        const float o0 = col[D_CL * stride], o1 = col[(D_CL + 1) * stride], o2 = col[(D_CL + 2) * stride],
+                    o3 = col[(D_CL + 3) * stride];
+        const float a = inside ? -expm1f(-softplusf_(o3) * s.w) * fminf(S, 1.f) : 0.f;
+        v = make_float4(sigmoidf_(o0), sigmoidf_(o1), sigmoidf_(o2), a);
+      }
+      if (threadIdx.x < SB) sOut[threadIdx.x] = v;
+      __syncthreads();
+      if (warp == 0) composite_rays(T, sOut, sT, it * RB, RB);
+      __syncthreads();
+      if (active) g4 = sOut[threadIdx.x];
+      if (__ballot_sync(0xffffffffu, active && inside) == 0u) continue;   // no live slot in the warp
+    }
     active = active && inside;
     if (active) {
       // ---------------- alpha, rgb, sigma
@@ -722,13 +816,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
       warp_back<kWidth, kResGammaPad>(sW + PL.r1, kPadRow, wcol, stride, b1, -1, R_DGAM, true);
       wgrad64(wcol, stride, R_GAM, kResGammaPad, b1, acc, Ly.r1, Ly.r1b, true);
       {  // per-frame sums of delta1 (for W_Omega): lane owns rows lane, lane + 32
-        const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
         const float *d0 = wcol + (b1 + lane) * stride, *d1 = wcol + (b1 + lane + 32) * stride;
         int cur = -1;
         float s0 = 0.f, s1 = 0.f;
         for (int sI = 0; sI < 32; ++sI) {
-          const uint32_t jj = j0 + sI;
-          if (jj >= n) break;
+          const uint32_t jj = q0 + sI;
+          if (jj >= n || (FUSED && (uint32_t)(warp * 32 + sI) >= SB)) break;
           const int fr = (int)T.frame_id[ray_of(T, jj)];
           if (fr != cur) {
             if (cur >= 0) {
@@ -831,8 +924,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) train_bwd_kernel(FieldParams P
     if (T.dG) {
       // dL/dG_i of each frame: dR_i += dp_i x^T, dt_i += dp_i over the warp's 32 samples;
       // lane owns 9 of the 24 x 12 entries and sums them per run of equal frames
-      const uint32_t j0 = it * step + blockIdx.x * blockDim.x + warp * 32;
-      const int fl = j0 + lane < n ? (int)T.frame_id[ray_of(T, j0 + lane)] : -1;
+      const int fl = qv ? (int)T.frame_id[r] : -1;
       const int f0 = __shfl_sync(0xffffffffu, fl, 0);
       if (__all_sync(0xffffffffu, fl == f0) && f0 >= 0) {
         // one frame in the warp: C[3i + r][c] = sum_s dp_i[s][r] (x_s, y_s, z_s, 1)[c] as one
@@ -1133,22 +1225,35 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
                                                                      s->bmax[1], s->bmax[2]);
   NR_CHECK_CUDA(cudaGetLastError());
   const size_t smem_f = sizeof(float) * T.pl.total;
-  NR_CHECK_CUDA(cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
-  train_fwd_kernel<<<blocks, kFwdThreads, smem_f, st>>>(P, T);
-  NR_CHECK_CUDA(cudaGetLastError());
-  train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
-  NR_CHECK_CUDA(cudaGetLastError());
+  // a step whose rays fit a backward block whole runs forward, compositing and backward in one
+  // kernel (train_bwd_kernel<true>); else the forward and the compositing adjoint run first
+  const bool fused = !fwd_only && b->n_samples <= (uint32_t)kBwdThreads;
+  if (!fused) {
+    NR_CHECK_CUDA(cudaFuncSetAttribute(train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+    train_fwd_kernel<<<blocks, kFwdThreads, smem_f, st>>>(P, T);
+    NR_CHECK_CUDA(cudaGetLastError());
+    train_composite_kernel<<<(b->n_rays + 255) / 256, 256, 0, st>>>(T);
+    NR_CHECK_CUDA(cudaGetLastError());
+    launched += 2;
+  }
   if (fwd_only) {
-    count_launches(launched + 4);
+    count_launches(launched + 2);
     if (loss_out) {
       NR_CHECK_CUDA(cudaMemcpyAsync(loss_out, s->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st));
       NR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
     return NR_OK;
   }
-  const size_t smem_b = sizeof(float) * (T.pl.total + (dG_smem ? n_dG : 0));
-  NR_CHECK_CUDA(cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  train_bwd_kernel<<<blocks, kBwdThreads, smem_b, st>>>(P, T);
+  const size_t smem_b = sizeof(float) * (T.pl.total + (dG_smem ? n_dG : 0)) + (fused ? kBwdThreads * 20 : 0);
+  if (fused) {
+    NR_CHECK_CUDA(
+        cudaFuncSetAttribute(train_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    train_bwd_kernel<true><<<blocks, kBwdThreads, smem_b, st>>>(P, T);
+  } else {
+    NR_CHECK_CUDA(
+        cudaFuncSetAttribute(train_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    train_bwd_kernel<false><<<blocks, kBwdThreads, smem_b, st>>>(P, T);
+  }
   NR_CHECK_CUDA(cudaGetLastError());
   reduce_acc_kernel<<<(A + 255) / 256, 256, 0, st>>>(s->t_wacc, (int)n_acc, A, s->t_red);
   ScatterArgs sa{};
@@ -1167,7 +1272,7 @@ extern "C" nr_status nr_train_step(nr_subject *s, const nr_train_batch *b, float
   }
   scatter_mlp_kernel<<<(sa.m.n_mlp + 255) / 256, 256, 0, st>>>(s->t_red, sa, s->g_mlp);
   NR_CHECK_CUDA(cudaGetLastError());
-  launched += 7;
+  launched += 5;   // samples, backward, reduction, two scatters
   if (refine && (r = launch_refine_bwd(s, s->f_omega, 3 * kBones, s->f_root, 3, (int)s->n_frames, s->f_dG,
                                        s->t_red + s->lay.total, s->g_ref, st)) != NR_OK)
     return r;
