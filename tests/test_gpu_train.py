@@ -100,6 +100,20 @@ def test_gradients_match_oracle():
         assert _rel(grads[g], ref[g]) <= TOL[g], (g, _rel(grads[g], ref[g]))
 
 
+def test_rays_longer_than_a_block_take_the_separate_kernels():
+    """A step whose rays hold more samples than a backward block has threads (400 > 384) runs the
+    forward, the compositing adjoint and the backward as separate kernels (the backward
+    recomputing the forward); its loss and gradients meet the same bounds against the oracle."""
+    subj, frames, batch, tgt = _setup(n_rays=48, S=400, seed=33)
+    loss, grads, _, _ = _gpu_step(subj, frames, batch, tgt, 400, 79, grad_only=True)
+    ref_loss, ref = _oracle_grads(subj, frames, batch, tgt, 400, 79)
+    assert abs(loss - ref_loss) <= 1e-5 * max(1.0, ref_loss), (loss, ref_loss)
+    print("S = 400: relative L2 per group:", {g: _rel(grads[g], ref[g]) for g in GROUPS})
+    for g in GROUPS:
+        assert np.linalg.norm(ref[g]) > 0, g
+        assert _rel(grads[g], ref[g]) <= TOL[g], (g, _rel(grads[g], ref[g]))
+
+
 def _linear_table(subj, levels=(4, 8), log2_t=10, seed=0):
     """Dense levels holding a linear function of the vertex position: the encoding is
     linear in x_final, with no kink at cell faces."""
