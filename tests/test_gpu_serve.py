@@ -30,14 +30,14 @@ def _requests(n, seed):
         cam = synth.camera(res, res, 1.25 * res, synth.random_eye(rng), int(rng.choice([16, 32])), 0.5, 4.5)
         aa, rt = synth.random_pose(rng)
         out.append(dict(subject=int(rng.integers(3)), cam=cam, aa=aa, rt=rt,
-                        mlp=["f32", "bf16"][k % 2], occ=bool(k % 3 != 0)))
+                        mlp=["f32", "bf16", "f32", "fp8"][k % 4], occ=bool(k % 3 != 0)))
     return out
 
 
 @pytest.mark.parametrize("order", ["edf", "smallest_first", "fifo"])
 def test_mix_equals_alone(subjects, order):
     """Under every dispatch policy each request of the mix equals the same request rendered
-    alone, bit for bit (bf16 requests on the tcgen05 pipeline included)."""
+    alone, bit for bit (bf16 and fp8 requests on the tcgen05 pipeline included)."""
     nr = nrmod()
     subs = [nr.Subject(s) for s in subjects]
     srv = nr.Server(max_bytes=8 << 30, max_slots=6)

@@ -63,17 +63,18 @@ def test_ws_psnr_against_oracle_and_agreement(tiny_structured, frame_structured,
         assert np.abs(a - b).max() <= 2e-2 and psnr(a, b) >= 55.0, (np.abs(a - b).max(), psnr(a, b))
 
 
-def test_ws_without_residual_and_two_hidden_layers(tiny_structured):
+@pytest.mark.parametrize("mlp", ["bf16", "fp8"])
+def test_ws_without_residual_and_two_hidden_layers(tiny_structured, mlp):
     # the tiny workload's canonical MLP has two hidden layers; with MLP_res off the pipeline runs
-    # only the canonical layers (another layer count per tile)
+    # only the canonical layers (another layer count per tile, and for fp8 another scale table)
     nr = nrmod()
     cfg = dict(tiny_structured)
     cfg["subject"] = dict(cfg["subject"], res_enabled=0)
     cam = cfg["camera"]
-    a, b = _pair(nr, cfg, cam, "bf16", "f32", False)
+    a, b = _pair(nr, cfg, cam, mlp, "f32", False)
     ref = oracle_render(cfg["subject"], cfg["pose"], cam, False).reshape(a.shape)
     assert psnr(a, ref) >= 50.0, psnr(a, ref)
-    assert psnr(a, b) >= 55.0
+    assert psnr(a, b) >= (55.0 if mlp == "bf16" else 45.0), psnr(a, b)
 
 
 def test_ws_query_ragged_tail_and_warp_outputs(tiny_structured):
