@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16"])
+    p.add_argument("--mlp", default="bf16", choices=["f32", "bf16", "f16", "fp8"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mma", choices=["pipeline", "tcgen05", "sync", "sync2"], default="pipeline",
                    help="bf16/f16 MLP path: the warp-specialised tcgen05 pipeline (default), tcgen05 with one "
@@ -503,10 +503,10 @@ def run_reference(a):
 # Per frame of the frame workload, from one ncu capture of the four field launches of a frame on
 # the default bf16 path, valid while the kernel sources have the SHA-256 given: DRAM bytes read +
 # written, and the bytes of the L1 sectors the global loads touched.
-FIELD_CAPTURE = {"sha256": "9a0d4cf11f6e722e92bcdebff8d73a9653abace41079a1fa122d1a7d93c8f0fc",
-                 "dram_bytes_per_frame": 152326912 + 54962944,
-                 "l1_sector_bytes_per_frame": 473859931 * 32,
-                 "l2_bytes_per_frame": 4513488608,
+FIELD_CAPTURE = {"sha256": "7e0b535bae2ce384af3cb894fd1a2309209b70e52460e794ccbd53d2e84dea07",
+                 "dram_bytes_per_frame": 152433152 + 55934976,
+                 "l1_sector_bytes_per_frame": 473845496 * 32,
+                 "l2_bytes_per_frame": 4518552640,
                  "live_samples_per_frame": 6173672}
 FIELD_SOURCES = ["field_ws.cu", "gather.cuh", "t5.cuh", "field.cuh", "mma.cuh", "common.cuh", "render.cuh"]
 
@@ -677,16 +677,20 @@ def run_ours(a):
                      "achieved": req_ach, "peak": req_bytes / t_req, "frac": req_ach / (req_bytes / t_req)}
     mlp_flops = mlp_flops_per_sample(s)
     mlp_tflops = mlp_flops * live / (field_ms / 1000.0) / 1e12
-    mlp_peak = peaks.get("bf16_tflops", 1900.0)
-    mlp_peak_sus = peaks.get("bf16_tflops_sustained", 1700.0)
+    # fp8 operands: the measured bf16 peak times the nominal fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s)
+    ratio = 2.0 if a.mlp == "fp8" else 1.0
+    mlp_peak = ratio * peaks.get("bf16_tflops", 1900.0)
+    mlp_peak_sus = ratio * peaks.get("bf16_tflops_sustained", 1700.0)
     kernel_name = {"pipeline": "field_ws_kernel (warp-specialised tcgen05)", "tcgen05": "field_t5_kernel",
                    "sync": "field_tc_kernel (mma.sync)", "sync2": "field_tc_kernel (mma.sync, two m-tiles)"}[a.mma]
     if a.mlp == "f32":
         kernel_name = "field_f32_kernel"
+    elif a.mlp == "fp8" and a.mma != "pipeline":
+        kernel_name = "field_fp8_kernel (mma.sync)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "bf16": "bf16", "f16": "f16"}[a.mlp], "data": "synthetic",
+        "dtype": {"f32": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8e4m3"}[a.mlp], "data": "synthetic",
         "config": {"workload": "frame_512x512_s128_occupancy", "image": [W, H], "samples_per_ray": 128,
                    "occupancy_grid": 128, "hash": "16x2 levels, 2^19 f16 entries, N 16..2048",
                    "mlp": f"32-64-64-64-4 {a.mlp}", "residual_mlp": f"6 PE bands, width 64, {a.mlp}",
@@ -730,11 +734,11 @@ def run_ours(a):
                           "achieved": mlp_tflops, "unit": "TFLOP/s", "flops_per_live_sample": mlp_flops,
                           "peak": mlp_peak, "frac": mlp_tflops / mlp_peak,
                           "peak_sustained": mlp_peak_sus, "frac_sustained": mlp_tflops / mlp_peak_sus,
-                          "peak_source": ("measured bf16 burst / sustained" if "bf16_tflops" in peaks
-                                          else "fallback"),
+                          "peak_source": (("measured bf16 burst / sustained" if "bf16_tflops" in peaks
+                                           else "fallback") + (" x 2 (nominal fp8 / bf16)" if ratio > 1 else "")),
                           "note": "algorithmic MLP flops over the whole field-kernel time: the gathers, not "
                                   "the tensor cores, bound this kernel"}
-                         if a.mlp in ("bf16", "f16") else None),
+                         if a.mlp in ("bf16", "f16", "fp8") else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * 12 * 4 + 24 * 3 * 4,
                 "d2h_bytes_per_step": n_rays * 16},
         "train_step": train,

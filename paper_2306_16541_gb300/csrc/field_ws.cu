@@ -57,7 +57,10 @@ constexpr uint32_t kWsAcc = 0, kWsAct = 64, kWsOne = 96, kWsGam = 104;
 constexpr int kWsBiasTile = 64 * 128;     // bytes of one bias tile: 64 rows of one swizzled 128-byte row
 constexpr int kWsMaxLayers = 5 + kMaxHidden + 1;
 constexpr unsigned long long kWsTimeoutNs = 500000000ull;
-constexpr int kWsF8Inv = kWsMaxLayers * (1 + 64);   // fp8 tier: offset of 1 / s_a (gamma, encoding) in its table
+// The fp8 tier's table in shared memory (floats): m' per layer, then b' [layer][64] from a
+// 16-byte aligned offset (read as float4), then 1 / s_a of gamma and of the encoding.
+constexpr int kWsF8Bias = (kWsMaxLayers + 3) & ~3;
+constexpr int kWsF8Inv = kWsF8Bias + kWsMaxLayers * 64;
 
 // One layer as the issuing thread sends it: nk K-steps of A (TMEM column a_col) x B (weights at
 // byte offset b_off of the shared blob), then nk2 K-steps of a second pair into the same
@@ -286,10 +289,9 @@ __device__ __forceinline__ void ws_relu_layer_f8(uint32_t my, float m, const flo
     uint32_t p[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int c = 32 * h + 4 * i;
-      p[i] = e4m3x4<true>(fmaf(__uint_as_float(v[4 * i]), m, b[c]), fmaf(__uint_as_float(v[4 * i + 1]), m, b[c + 1]),
-                          fmaf(__uint_as_float(v[4 * i + 2]), m, b[c + 2]),
-                          fmaf(__uint_as_float(v[4 * i + 3]), m, b[c + 3]));
+      const float4 bb = reinterpret_cast<const float4 *>(b)[8 * h + i];   // one broadcast load per 4 columns
+      p[i] = e4m3x4<true>(fmaf(__uint_as_float(v[4 * i]), m, bb.x), fmaf(__uint_as_float(v[4 * i + 1]), m, bb.y),
+                          fmaf(__uint_as_float(v[4 * i + 2]), m, bb.z), fmaf(__uint_as_float(v[4 * i + 3]), m, bb.w));
     }
     tm_st8(my + kWsAct + 8 * h, p);
   }
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
   uint64_t *sBar = reinterpret_cast<uint64_t *>(sG + kPoseSmem);         // input ready[G], done[G], drain[G]
   WsLayer *sLay = reinterpret_cast<WsLayer *>(sBar + 3 * kWsGroups);
   uint32_t *sTmem = reinterpret_cast<uint32_t *>(sLay + kWsMaxLayers);
-  float *sF8 = reinterpret_cast<float *>(sTmem + 4);   // fp8 tier: m' per layer, then b' [layer][64]
+  float *sF8 = reinterpret_cast<float *>(sTmem + 4);   // fp8 tier's table (16-byte aligned)
   constexpr bool F8 = kIsF8<T>;
 
   {  // a block with no tile leaves before any set-up (the live count is known only here)
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       };
       for (int i = tid; i < nl * kWidth; i += blockDim.x) {
         const int li = i / kWidth, n = i % kWidth;
-        sF8[kWsMaxLayers + i] = bias_of(li, n) * sc[kF8SlotWs + 2 * li + 1];
+        sF8[kWsF8Bias + i] = bias_of(li, n) * sc[kF8SlotWs + 2 * li + 1];
       }
       if (tid < nl) sF8[tid] = sc[kF8SlotWs + 2 * tid] * sc[kF8SlotWs + 2 * tid + 1];
       if (tid == 0) {   // 1 / s_a of gamma and of the hash encoding (the inputs the workers quantise)
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
           float o3[4];
           tm_ld4(my + kWsAcc, o3);
           if constexpr (F8) {
-            const float *b8 = sF8 + kWsMaxLayers + 4 * kWidth;
+            const float *b8 = sF8 + kWsF8Bias + 4 * kWidth;
             f0 += fmaf(o3[0], sF8[4], b8[0]);
             f1 += fmaf(o3[1], sF8[4], b8[1]);
             f2 += fmaf(o3[2], sF8[4], b8[2]);
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
             f2 += o3[2] + sBias[bl.r5 + 2];
           }
         } else if constexpr (F8) {
-          ws_relu_layer_f8(my, sF8[li], sF8 + kWsMaxLayers + li * kWidth);
+          ws_relu_layer_f8(my, sF8[li], sF8 + kWsF8Bias + li * kWidth);
         } else {
           ws_relu_layer<T>(my);
         }
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) field_ws_kernel(FieldParams P, 
       if constexpr (F8) {
         const int lo = n_layers - 1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) o[k] = fmaf(o[k], sF8[lo], sF8[kWsMaxLayers + lo * kWidth + k]);
+        for (int k = 0; k < 4; ++k) o[k] = fmaf(o[k], sF8[lo], sF8[kWsF8Bias + lo * kWidth + k]);
       } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k) o[k] += sBias[bl.cl + k];
