@@ -287,10 +287,13 @@ __global__ void __launch_bounds__(256) march_round_kernel(CamParams cam, MarchPa
   float h[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) h[q] = __fdiv_rn(__fsub_rn(mp.bmax[q], mp.bmin[q]), (float)G);
-  auto live = [&](uint32_t i, float x[3]) -> bool {
+  auto pos = [&](uint32_t i, float x[3]) {
     const float t = __fadd_rn(lo, __fmul_rn(__fadd_rn((float)i, 0.5f), D));
 #pragma unroll
     for (int q = 0; q < 3; ++q) x[q] = __fadd_rn(o[q], __fmul_rn(t, d[q]));
+  };
+  auto live = [&](uint32_t i, float x[3]) -> bool {
+    pos(i, x);
     if (!mp.bits) return true;
     int c[3];
 #pragma unroll
@@ -303,10 +306,17 @@ __global__ void __launch_bounds__(256) march_round_kernel(CamParams cam, MarchPa
   };
   const uint32_t i0 = st0 & ~kRayDone;
   uint32_t count = 0, i_end = S;                      // a ray that misses the box has no slots left
+  uint64_t m0 = 0u, m1 = 0u;                          // live flags of slots i0 .. i0 + 63, i0 + 64 .. i0 + 127
   if (active) {
     float x[3];
     uint32_t i = i0;
-    for (; i < S && count < k; ++i) count += live(i, x) ? 1u : 0u;
+    for (; i < S && count < k; ++i) {
+      const bool lv = live(i, x);
+      count += lv ? 1u : 0u;
+      const uint32_t e = i - i0;
+      if (lv && e < 64u) m0 |= 1ull << e;
+      else if (lv && e < 128u) m1 |= 1ull << (e - 64u);
+    }
     i_end = i;
   }
   uint32_t incl = count;
@@ -329,9 +339,23 @@ __global__ void __launch_bounds__(256) march_round_kernel(CamParams cam, MarchPa
   }
   if (count) {
     uint32_t w = off;
-    for (uint32_t i = i0; w < off + count; ++i) {
-      float x[3];
-      if (live(i, x)) samp[w++] = make_float4(x[0], x[1], x[2], D);
+    if (i_end - i0 <= 128u) {   // the flags hold every slot tested: only positions are recomputed
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint64_t bits = q ? m1 : m0;
+        while (bits) {
+          const uint32_t e = 64u * q + (uint32_t)(__ffsll((long long)bits) - 1);
+          bits &= bits - 1u;
+          float x[3];
+          pos(i0 + e, x);
+          samp[w++] = make_float4(x[0], x[1], x[2], D);
+        }
+      }
+    } else {
+      for (uint32_t i = i0; w < off + count; ++i) {
+        float x[3];
+        if (live(i, x)) samp[w++] = make_float4(x[0], x[1], x[2], D);
+      }
     }
   }
 }
