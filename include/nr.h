@@ -128,7 +128,11 @@ nr_status nr_destroy(nr_subject *s);
  * as zero for the residual MLP.  With a pose refiner installed
  * (nr_set_pose_refiner) and joint angles given, G is that of the refined pose,
  * computed on the device, and is re-derived after every training step that
- * updates the refiner.  Host pointers. */
+ * updates the refiner.  Host pointers, read during the call.  The call does
+ * not wait for the device: the transforms travel as a kernel argument and the
+ * device work is queued on `stream`.  A later call that uses the pose on
+ * another stream waits for that work (an event), except inside a stream
+ * capture, which the caller must order after the pose. */
 nr_status nr_set_pose(nr_subject *s, const float *axis_angle, const float *root_t,
                       uint32_t flags, void *stream);
 
@@ -462,8 +466,9 @@ nr_status nr_canonical_occupancy(nr_subject *s, uint32_t *bits_out);
  * [5] the mean number of weight-volume bone channels the field read per live
  * sample (channels whose support holds the candidate; the default bf16/f16
  * pipeline counts them, other paths report 0).
- * ms_out holds 6 floats.  CUDA events on the render's stream bracket every launch; this
- * call waits for them.  NR_ESTATE if no profiled render has run. */
+ * ms_out holds 6 floats.  A CUDA event on the render's stream marks every
+ * boundary between its launches (a stage's time runs from the mark before its
+ * launch to the mark after it); this call waits for them.  NR_ESTATE if no profiled render has run. */
 nr_status nr_stage_times(nr_subject *s, float *ms_out);
 
 /* Number of CUDA kernels this library has launched since it was loaded

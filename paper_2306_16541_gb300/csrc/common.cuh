@@ -177,6 +177,10 @@ struct nr_subject {
   bool pose_set = false;
   bool pose_matrices = false;        // the pose was given as G (NR_POSE_MATRICES)
   bool pose_dirty = false;           // d_G (and the posed bitfield) must be re-derived
+  bool d_G_host = false;             // d_G holds h_G (not a refined pose)
+  cudaEvent_t pose_ev = nullptr;     // recorded after the last nr_set_pose's device work
+  cudaStream_t pose_stream = nullptr;  // the stream of that work
+  bool pose_ev_live = false;
   float h_G[24 * 12];                // host forward kinematics of the estimated pose
   float h_omega[24 * 3];
   float h_root[3] = {0.f, 0.f, 0.f};
@@ -224,11 +228,11 @@ struct nr_subject {
   size_t stage_cap = 0;
   float4 *ray_state = nullptr;       // [max rays] running (C, T) of round-based early termination
   uint32_t *ray_next = nullptr;      // [max rays] next slot of each ray, top bit = retired
-  // stage profiling (NR_RENDER_PROFILE): a start/end event pair per launch, tagged by stage
+  // stage profiling (NR_RENDER_PROFILE): an event per launch boundary, tagged by the stage it ends
   static constexpr int kProfEvents = 512;
   cudaEvent_t prof_ev[kProfEvents] = {};
-  int prof_stage[kProfEvents / 2] = {};
-  int prof_used = 0;                 // event pairs recorded by the last profiled render
+  int prof_stage[kProfEvents] = {};
+  int prof_used = 0;                 // events recorded by the last profiled render
   bool prof_overflow = false;
   // training workspace (grow-only)
   size_t tw_samples = 0;             // capacity of t_samp / t_out / t_T
@@ -264,6 +268,7 @@ nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const f
                                 cudaStream_t st);
 nr_status ensure_occupancy(nr_subject *s, cudaStream_t st);    // posed grid of the current pose (kOccGrid)
 nr_status ensure_pose(nr_subject *s, cudaStream_t st);         // d_G (refined if MLP_theta is on), bitfields
+nr_status after_pose(nr_subject *s, cudaStream_t st);          // orders st after the last nr_set_pose
 nr_status launch_refine_fk(const nr_subject *s, const float *omega, int omega_stride, const float *root,
                            int root_stride, int n, float *G, float *omega_o, int omega_o_stride, cudaStream_t st);
 nr_status launch_refine_bwd(const nr_subject *s, const float *omega, int omega_stride, const float *root,

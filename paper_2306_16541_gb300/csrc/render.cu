@@ -256,8 +256,12 @@ __global__ void __launch_bounds__(256) composite_kernel(const uint2 *__restrict_
 // single pass's, so the image is identical.
 constexpr uint32_t kRayDone = 0x80000000u;
 
-__global__ void init_rays_kernel(uint32_t n, float4 *__restrict__ state, uint32_t *__restrict__ next) {
+// Also clears the live-sample counter for the first round (the round's composite clears it for
+// the next), so that no memset sits between the launches of a frame.
+__global__ void init_rays_kernel(uint32_t n, float4 *__restrict__ state, uint32_t *__restrict__ next,
+                                 uint32_t *__restrict__ counter) {
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) *counter = 0u;
   if (r < n) {
     state[r] = make_float4(0.f, 0.f, 0.f, 1.f);
     next[r] = 0u;
@@ -364,8 +368,9 @@ __global__ void __launch_bounds__(256) march_round_kernel(CamParams cam, MarchPa
 __global__ void __launch_bounds__(256) composite_round_kernel(const uint2 *__restrict__ ray_range,
                                                               const float4 *__restrict__ so, uint32_t n_rays,
                                                               float t_min, uint32_t S, float4 *__restrict__ state,
-                                                              uint32_t *__restrict__ next) {
+                                                              uint32_t *__restrict__ next, uint32_t *__restrict__ counter) {
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) *counter = 0u;   // the round's field launch has read it: cleared for the next march
   if (r >= n_rays) return;
   const uint32_t nx = next[r];
   if (nx & kRayDone) return;
@@ -568,20 +573,16 @@ nr_status render_rays(const nr_subject *s, const FieldParams &P, const uint32_t 
   }
   mp.grid = (int)s->occ_grid;
   mp.bits = opts->use_occupancy ? bits : nullptr;
-  auto mark = [&](int stage, bool begin) -> cudaError_t {
+  // One event per launch boundary: mark(stage) closes the interval since the previous mark as
+  // that stage's; mark(-1) opens a run of back-to-back launches (its interval is not counted).
+  auto mark = [&](int stage) -> cudaError_t {
     if (!prof) return cudaSuccess;
-    if (begin) {
-      if (prof->used >= prof->cap) return cudaSuccess;
-      prof->stage[prof->used] = stage;
-      return cudaEventRecord(prof->ev[2 * prof->used], st);
-    }
     if (prof->used >= prof->cap) {
       prof->overflow = true;
       return cudaSuccess;
     }
-    const cudaError_t e = cudaEventRecord(prof->ev[2 * prof->used + 1], st);
-    prof->used += 1;
-    return e;
+    prof->stage[prof->used] = stage;
+    return cudaEventRecord(prof->ev[prof->used++], st);
   };
   nr_status r;
   const uint32_t n_rounds = rounds ? (S + k - 1) / k : 1;
@@ -591,35 +592,34 @@ nr_status render_rays(const nr_subject *s, const FieldParams &P, const uint32_t 
     mp.ray0 = r0;
     mp.ray_end = r0 + nr_;
     if (rounds) {
-      init_rays_kernel<<<nb, 256, 0, st>>>(nr_, w.state, w.next);
+      init_rays_kernel<<<nb, 256, 0, st>>>(nr_, w.state, w.next, w.counter);
       count_launches(1);
     }
     for (uint32_t round = 0; round < n_rounds; ++round) {
-      NR_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(uint32_t), st));
-      NR_CHECK_CUDA(mark(0, true));
+      if (!rounds) NR_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(uint32_t), st));
+      if (round == 0 || !rounds) NR_CHECK_CUDA(mark(-1));
       if (rounds)
         march_round_kernel<<<nb, 256, 0, st>>>(C, mp, k, w.samp, w.ray_range, w.counter, w.total, w.next);
       else
         march_kernel<<<nb, 256, 0, st>>>(C, mp, w.samp, w.ray_range, w.counter);
       NR_CHECK_CUDA(cudaGetLastError());
-      NR_CHECK_CUDA(mark(0, false));
       if (!rounds && w.total) {
         add_u32_kernel<<<1, 1, 0, st>>>(w.total, w.counter);
         count_launches(1);
       }
-      NR_CHECK_CUDA(mark(1, true));
+      NR_CHECK_CUDA(mark(0));
       if ((r = launch_field(P, opts->mlp_dtype, kModeRender, w.samp, 0, w.counter, (float *)w.samp_out, s->device, st,
                             mma_path)) != NR_OK)
         return r;
-      NR_CHECK_CUDA(mark(1, false));
-      NR_CHECK_CUDA(mark(2, true));
+      NR_CHECK_CUDA(mark(1));
       if (rounds)
-        composite_round_kernel<<<nb, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, S, w.state, w.next);
+        composite_round_kernel<<<nb, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, S, w.state, w.next,
+                                                   w.counter);
       else
         composite_kernel<<<nb, 256, 0, st>>>(w.ray_range, w.samp_out, nr_, opts->t_min, cam->bg[0], cam->bg[1],
                                              cam->bg[2], dst + r0);
       NR_CHECK_CUDA(cudaGetLastError());
-      NR_CHECK_CUDA(mark(2, false));
+      NR_CHECK_CUDA(mark(2));
       count_launches(3);
     }
     if (rounds) {
@@ -697,7 +697,7 @@ extern "C" nr_status nr_render(nr_subject *s, const nr_camera *cam, const nr_ren
       if (!s->prof_ev[i]) NR_CHECK_CUDA(cudaEventCreate(&s->prof_ev[i]));
     pr.ev = s->prof_ev;
     pr.stage = s->prof_stage;
-    pr.cap = nr_subject::kProfEvents / 2;
+    pr.cap = nr_subject::kProfEvents;
     NR_CHECK_CUDA(cudaMemsetAsync(s->counter + 8, 0, 2 * sizeof(uint32_t), st));
   }
   FrameWork w{};
@@ -731,12 +731,13 @@ extern "C" nr_status nr_stage_times(nr_subject *s, float *ms) {
     return NR_ESTATE;
   }
   NR_CHECK_CUDA(cudaSetDevice(s->device));
-  NR_CHECK_CUDA(cudaEventSynchronize(s->prof_ev[2 * s->prof_used - 1]));
+  NR_CHECK_CUDA(cudaEventSynchronize(s->prof_ev[s->prof_used - 1]));
   float acc[3] = {0.f, 0.f, 0.f};
   int field_launches = 0;
-  for (int i = 0; i < s->prof_used; ++i) {
+  for (int i = 1; i < s->prof_used; ++i) {
+    if (s->prof_stage[i] < 0) continue;
     float t = 0.f;
-    NR_CHECK_CUDA(cudaEventElapsedTime(&t, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]));
+    NR_CHECK_CUDA(cudaEventElapsedTime(&t, s->prof_ev[i - 1], s->prof_ev[i]));
     acc[s->prof_stage[i]] += t;
     field_launches += s->prof_stage[i] == 1;
   }

@@ -97,8 +97,8 @@ struct FrameWork {
 
 // Start/end CUDA-event pairs recorded around each launch of a profiled render.
 struct Prof {
-  cudaEvent_t *ev;                // 2 * cap events
-  int *stage;                     // [cap] 0 march, 1 field, 2 composite
+  cudaEvent_t *ev;                // [cap] events, one per launch boundary
+  int *stage;                     // [cap] the stage ending at each: 0 march, 1 field, 2 composite, -1 none
   int cap, used;
   bool overflow;
 };

@@ -678,6 +678,7 @@ static void free_subject(nr_subject *s) {
     if (p) cudaFree(p);
   for (cudaEvent_t &e : s->prof_ev)
     if (e) cudaEventDestroy(e);
+  if (s->pose_ev) cudaEventDestroy(s->pose_ev);
   s->magic = 0;
   delete s;
 }
@@ -826,6 +827,20 @@ extern "C" nr_status nr_destroy(nr_subject *s) {
   return NR_OK;
 }
 
+// The pose of one nr_set_pose call, passed by value as a kernel argument (1,452 bytes): the
+// launch copies it when it is queued, so the call neither stages a host copy nor waits for the
+// device.
+struct PoseUpload {
+  float G[kBones * 12];
+  float omega[kBones * 3 + 3];   // joint angles, then the root translation
+};
+
+__global__ void __launch_bounds__(128) store_pose_kernel(const PoseUpload u, float *__restrict__ G,
+                                                         float *__restrict__ omega) {
+  for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) G[i] = u.G[i];
+  for (int i = threadIdx.x; i < kBones * 3 + 3; i += blockDim.x) omega[i] = u.omega[i];
+}
+
 extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *root_t, uint32_t flags, void *stream) {
   NR_REQUIRE(subject_ok(s), "nr_set_pose: invalid handle");
   NR_REQUIRE(aa, "nr_set_pose: NULL pose");
@@ -843,29 +858,55 @@ extern "C" nr_status nr_set_pose(nr_subject *s, const float *aa, const float *ro
     for (int k = 0; k < 3; ++k) s->h_root[k] = root_t ? root_t[k] : 0.f;
   }
   s->pose_matrices = (flags & NR_POSE_MATRICES) != 0;
-  NR_CHECK_CUDA(cudaMemcpyAsync(s->d_omega, s->h_omega, sizeof(float) * 3 * s->K, cudaMemcpyHostToDevice, st));
-  NR_CHECK_CUDA(cudaMemcpyAsync(s->d_omega + 3 * s->K, s->h_root, sizeof(float) * 3, cudaMemcpyHostToDevice, st));
+  nr_status r = after_pose(s, st);   // the previous pose's work, if on another stream, comes first
+  if (r != NR_OK) return r;
+  PoseUpload u;
+  memcpy(u.G, s->h_G, sizeof(u.G));
+  memcpy(u.omega, s->h_omega, sizeof(float) * 3 * kBones);
+  memcpy(u.omega + 3 * kBones, s->h_root, sizeof(float) * 3);
+  store_pose_kernel<<<1, 128, 0, st>>>(u, s->d_G, s->d_omega);
+  NR_CHECK_CUDA(cudaGetLastError());
+  count_launches(1);
+  s->d_G_host = true;
   s->pose_set = true;
   s->pose_dirty = true;
   s->bias_dirty = true;
-  nr_status r = ensure_pose(s, st);
-  // h_G / h_omega / h_root are reused by the next call: the copies must have read them
-  NR_CHECK_CUDA(cudaStreamSynchronize(st));
-  return r;
+  s->pose_ev_live = false;
+  if ((r = ensure_pose(s, st)) != NR_OK) return r;
+  if (!s->pose_ev) NR_CHECK_CUDA(cudaEventCreateWithFlags(&s->pose_ev, cudaEventDisableTiming));
+  NR_CHECK_CUDA(cudaEventRecord(s->pose_ev, st));
+  s->pose_stream = st;
+  s->pose_ev_live = true;
+  return NR_OK;
+}
+
+// A consumer of the pose on another stream than the last nr_set_pose waits for that call's
+// device work.  Under a stream capture the wait is left out (a capture may not wait on an event
+// recorded outside it): the caller orders the capture after the pose.
+nr_status nr::after_pose(nr_subject *s, cudaStream_t st) {
+  if (!s->pose_ev_live || st == s->pose_stream) return NR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NR_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusNone) NR_CHECK_CUDA(cudaStreamWaitEvent(st, s->pose_ev, 0));
+  return NR_OK;
 }
 
 // Derives the device transforms of the current pose: the refined pose when
 // MLP_theta is on (and the pose came as joint angles), else the host forward
 // kinematics; then the posed occupancy of the subject's source.
 nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
+  nr_status r = after_pose(s, st);
+  if (r != NR_OK) return r;
   if (!s->pose_dirty || !s->pose_set) return NR_OK;
-  nr_status r;
   if (s->ref_layers && !s->pose_matrices) {
     if ((r = launch_refine_fk(s, s->d_omega, 3 * kBones, s->d_omega + 3 * kBones, 3, 1, s->d_G,
                               s->d_omega + 3 * kBones + 3, 3 * kBones, st)) != NR_OK)
       return r;
-  } else {
+    s->d_G_host = false;
+  } else if (!s->d_G_host) {   // the refiner was removed since: back to the host's transforms
     NR_CHECK_CUDA(cudaMemcpyAsync(s->d_G, s->h_G, sizeof(float) * 12 * s->K, cudaMemcpyHostToDevice, st));
+    NR_CHECK_CUDA(cudaStreamSynchronize(st));   // h_G is rewritten by the next nr_set_pose
+    s->d_G_host = true;
   }
   if (s->occ_source == kOccEllipsoids) {
     const int g = (int)s->occ_grid;
