@@ -132,7 +132,9 @@ nr_status nr_destroy(nr_subject *s);
  * not wait for the device: the transforms travel as a kernel argument and the
  * device work is queued on `stream`.  A later call that uses the pose on
  * another stream waits for that work (an event), except inside a stream
- * capture, which the caller must order after the pose. */
+ * capture, which the caller must order after the pose.  The reverse order is
+ * the caller's: a render still running on another stream reads the pose
+ * buffers this call rewrites, so order the call after it. */
 nr_status nr_set_pose(nr_subject *s, const float *axis_angle, const float *root_t,
                       uint32_t flags, void *stream);
 

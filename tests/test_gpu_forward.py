@@ -426,3 +426,39 @@ def test_f32_tensor_core_tier(tiny_structured, frame):
     assert rc == nr.NR_EUNSUPPORTED
     assert np.array_equal(qa[:, :4], qb[:, :4])
     assert np.abs(qa[:, 4:] - qb[:, 4:]).max() <= 1e-4 * max(1.0, np.abs(qb[:, 4:]).max())
+
+
+def test_pose_set_on_one_stream_reaches_renders_on_another(frame):
+    """nr_set_pose queues its device work and returns; a render or a transform read issued on
+    another stream right after it, with no host synchronisation between, must see that pose:
+    each image equals the one rendered with pose and render on the same stream, bit for bit,
+    and the transforms equal the oracle's forward kinematics.  (The other direction, a new pose
+    after a render still running on another stream, is the caller's to order.)"""
+    nr = nrmod()
+    cam = nr.make_camera(_small(frame["camera"], 64))
+    opts = nr.make_opts("bf16", "f16", True, 1e-4)
+    rng = np.random.default_rng(77)
+    poses = [synth.random_pose(rng) for _ in range(6)]
+    S = nr.Subject(frame["subject"])
+    try:
+        ref = []
+        for p in poses:
+            S.set_pose(*p)
+            ref.append(S.render(cam, opts).cpu().numpy())
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        outs = [torch.empty(cam.height, cam.width, 4, device="cuda") for _ in range(3 * len(poses))]
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            S.set_pose(*poses[i % len(poses)], stream=s1)
+            S.render(cam, opts, o, stream=s2)
+            s1.wait_stream(s2)      # the caller orders the next pose after a render that reads this one
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy(), ref[i % len(poses)]), i
+        s = frame["subject"]
+        for p in poses[:2]:
+            S.set_pose(*p, stream=s1)
+            G = S.pose_transforms()                 # legacy default stream, synchronous read
+            assert np.abs(G - fk.bone_transforms_f32(s["parents"], s["rest_joints"], *p)).max() <= 1e-6
+    finally:
+        S.close()
