@@ -114,7 +114,6 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
   for (int i = threadIdx.x; i < kBones * 12; i += blockDim.x) sG[i] = G[i];
   for (int i = threadIdx.x; i < kBones * 15; i += blockDim.x) sE[i] = E[i];
   const uint32_t n = (uint32_t)grid * grid * grid;
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   const float fg = (float)grid;
   const float h0 = __fdiv_rn(__fsub_rn(Bx, bx), fg);     // (bmax - bmin) / G
   const float h1 = __fdiv_rn(__fsub_rn(By, by), fg);
@@ -146,6 +145,9 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
     sC[4 * i + 3] = dev < 1e-4f ? rho * rho : INFINITY;
   }
   __syncthreads();
+  // blocks stride over the grid in steps of 256 cells, so the set-up above runs once per block
+  for (uint32_t c0 = blockIdx.x * blockDim.x; c0 < n; c0 += gridDim.x * blockDim.x) {
+  const uint32_t c = c0 + threadIdx.x;
   bool occ = false;
   if (c < n) {
     const int cx = (int)(c % grid), cy = (int)((c / grid) % grid), cz = (int)(c / (grid * grid));
@@ -183,6 +185,12 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
   }
   const unsigned word = __ballot_sync(0xffffffffu, occ);
   if ((threadIdx.x & 31) == 0 && c < n) bits[c >> 5] = word;
+  }
+}
+
+// Blocks of the posed-bitfield launch: eight 256-thread blocks per SM, striding over the cells.
+static unsigned bitfield_blocks(long n, int device) {
+  return (unsigned)std::min<long>((n + 255) / 256, 8L * num_sms(device));
 }
 
 // ------------------------------------------------------ bone support boxes
@@ -558,7 +566,7 @@ nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const f
   }
   const int g = (int)s->occ_grid;
   const long n = (long)g * g * g;
-  posed_bitfield_kernel<<<nblk(n, 256), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
+  posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
                                                       s->bmax[1], s->bmax[2], g, bits);
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
@@ -911,7 +919,7 @@ nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
   if (s->occ_source == kOccEllipsoids) {
     const int g = (int)s->occ_grid;
     const long n = (long)g * g * g;
-    posed_bitfield_kernel<<<nblk(n, 256), 256, 0, st>>>(s->d_G, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2],
+    posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(s->d_G, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2],
                                                         s->bmax[0], s->bmax[1], s->bmax[2], g, s->bits);
     NR_CHECK_CUDA(cudaGetLastError());
     count_launches(1);
