@@ -147,44 +147,44 @@ __global__ void __launch_bounds__(256) posed_bitfield_kernel(const float *__rest
   __syncthreads();
   // blocks stride over the grid in steps of 256 cells, so the set-up above runs once per block
   for (uint32_t c0 = blockIdx.x * blockDim.x; c0 < n; c0 += gridDim.x * blockDim.x) {
-  const uint32_t c = c0 + threadIdx.x;
-  bool occ = false;
-  if (c < n) {
-    const int cx = (int)(c % grid), cy = (int)((c / grid) % grid), cz = (int)(c / (grid * grid));
-    // y_k = bmin_k + ((j_k + 0.5) h_k)
-    const float y0 = __fadd_rn(bx, __fmul_rn(__fadd_rn((float)cx, 0.5f), h0));
-    const float y1 = __fadd_rn(by, __fmul_rn(__fadd_rn((float)cy, 0.5f), h1));
-    const float y2 = __fadd_rn(bz, __fmul_rn(__fadd_rn((float)cz, 0.5f), h2));
-    for (int i = 0; i < kBones && !occ; ++i) {
-      const float *sc = sC + 4 * i;
-      const float a0 = y0 - sc[0], a1 = y1 - sc[1], a2 = y2 - sc[2];
-      if (a0 * a0 + a1 * a1 + a2 * a2 > sc[3]) continue;
-      const float *g = sG + 12 * i;
-      const float *e = sE + 15 * i;
-      float v[3];
+    const uint32_t c = c0 + threadIdx.x;
+    bool occ = false;
+    if (c < n) {
+      const int cx = (int)(c % grid), cy = (int)((c / grid) % grid), cz = (int)(c / (grid * grid));
+      // y_k = bmin_k + ((j_k + 0.5) h_k)
+      const float y0 = __fadd_rn(bx, __fmul_rn(__fadd_rn((float)cx, 0.5f), h0));
+      const float y1 = __fadd_rn(by, __fmul_rn(__fadd_rn((float)cy, 0.5f), h1));
+      const float y2 = __fadd_rn(bz, __fmul_rn(__fadd_rn((float)cz, 0.5f), h2));
+      for (int i = 0; i < kBones && !occ; ++i) {
+        const float *sc = sC + 4 * i;
+        const float a0 = y0 - sc[0], a1 = y1 - sc[1], a2 = y2 - sc[2];
+        if (a0 * a0 + a1 * a1 + a2 * a2 > sc[3]) continue;
+        const float *g = sG + 12 * i;
+        const float *e = sE + 15 * i;
+        float v[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        // q_r = (((R_r0 y0) + (R_r1 y1)) + (R_r2 y2)) + t_r ; v_r = q_r - centre_r
-        const float q = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(g[4 * r], y0), __fmul_rn(g[4 * r + 1], y1)),
-                                            __fmul_rn(g[4 * r + 2], y2)),
-                                  g[4 * r + 3]);
-        v[r] = __fsub_rn(q, e[r]);
-      }
-      float s2[3];
+        for (int r = 0; r < 3; ++r) {
+          // q_r = (((R_r0 y0) + (R_r1 y1)) + (R_r2 y2)) + t_r ; v_r = q_r - centre_r
+          const float q = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(g[4 * r], y0), __fmul_rn(g[4 * r + 1], y1)),
+                                              __fmul_rn(g[4 * r + 2], y2)),
+                                    g[4 * r + 3]);
+          v[r] = __fsub_rn(q, e[r]);
+        }
+        float s2[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        // l_m = ((Q_m0 v0) + (Q_m1 v1)) + (Q_m2 v2) ; s_m = l_m / (r_m + dil)
-        const float l = __fadd_rn(__fadd_rn(__fmul_rn(e[3 + 3 * m], v[0]), __fmul_rn(e[3 + 3 * m + 1], v[1])),
-                                  __fmul_rn(e[3 + 3 * m + 2], v[2]));
-        s2[m] = __fdiv_rn(l, __fadd_rn(e[12 + m], dil));
+        for (int m = 0; m < 3; ++m) {
+          // l_m = ((Q_m0 v0) + (Q_m1 v1)) + (Q_m2 v2) ; s_m = l_m / (r_m + dil)
+          const float l = __fadd_rn(__fadd_rn(__fmul_rn(e[3 + 3 * m], v[0]), __fmul_rn(e[3 + 3 * m + 1], v[1])),
+                                    __fmul_rn(e[3 + 3 * m + 2], v[2]));
+          s2[m] = __fdiv_rn(l, __fadd_rn(e[12 + m], dil));
+        }
+        // ((s0 s0) + (s1 s1)) + (s2 s2) <= 1
+        const float q2 = __fadd_rn(__fadd_rn(__fmul_rn(s2[0], s2[0]), __fmul_rn(s2[1], s2[1])), __fmul_rn(s2[2], s2[2]));
+        occ = q2 <= 1.f;
       }
-      // ((s0 s0) + (s1 s1)) + (s2 s2) <= 1
-      const float q2 = __fadd_rn(__fadd_rn(__fmul_rn(s2[0], s2[0]), __fmul_rn(s2[1], s2[1])), __fmul_rn(s2[2], s2[2]));
-      occ = q2 <= 1.f;
     }
-  }
-  const unsigned word = __ballot_sync(0xffffffffu, occ);
-  if ((threadIdx.x & 31) == 0 && c < n) bits[c >> 5] = word;
+    const unsigned word = __ballot_sync(0xffffffffu, occ);
+    if ((threadIdx.x & 31) == 0 && c < n) bits[c >> 5] = word;
   }
 }
 
@@ -566,8 +566,9 @@ nr_status launch_posed_bitfield(const nr_subject *s, const float *G_dev, const f
   }
   const int g = (int)s->occ_grid;
   const long n = (long)g * g * g;
-  posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2], s->bmax[0],
-                                                      s->bmax[1], s->bmax[2], g, bits);
+  posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(G_dev, s->ellip, s->bmin[0], s->bmin[1],
+                                                                       s->bmin[2], s->bmax[0], s->bmax[1], s->bmax[2],
+                                                                       g, bits);
   NR_CHECK_CUDA(cudaGetLastError());
   count_launches(1);
   return NR_OK;
@@ -919,8 +920,9 @@ nr_status nr::ensure_pose(nr_subject *s, cudaStream_t st) {
   if (s->occ_source == kOccEllipsoids) {
     const int g = (int)s->occ_grid;
     const long n = (long)g * g * g;
-    posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(s->d_G, s->ellip, s->bmin[0], s->bmin[1], s->bmin[2],
-                                                        s->bmax[0], s->bmax[1], s->bmax[2], g, s->bits);
+    posed_bitfield_kernel<<<bitfield_blocks(n, s->device), 256, 0, st>>>(s->d_G, s->ellip, s->bmin[0], s->bmin[1],
+                                                                         s->bmin[2], s->bmax[0], s->bmax[1],
+                                                                         s->bmax[2], g, s->bits);
     NR_CHECK_CUDA(cudaGetLastError());
     count_launches(1);
   }
